@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""OverSketch benchmark: sketched A.B effective TFLOP/s (2mnl/t) on GB300.
+
+One step = one whole OverSketch product on the square workload
+(A 16384x65536, B 65536x16384 FP32 N(0,1) + rank-64 spike; b=1024, N=8,
+e=2; blocks {1,6} dropped): left sketch, right sketch (both emitting the GEMM
+dtype), masked block-sum GEMM with scale 1/k.  Inputs (8.6 GB) exceed L2, so
+no flush is needed between steps.  The plan (hash + bucket-CSR) is built once
+before timing, as the same S is reused across products.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|f32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a sample
+
+Multi-GPU (torchrun): every rank runs its own independent product (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sketched A·B effective TFLOP/s (2mnl/t) vs exact GEMM at stated Frobenius error"
+UNIT = "TFLOP/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------------
+
+def oracle_sample_time(w, rows: int, cols: int, reps: int = 1, inputs=None):
+    """Time the oracle (as it stands) on a rows x n x cols sample of the workload:
+    both sketches and the masked product in FP64 (the plan is built once,
+    untimed, as on the GPU).  Returns (seconds, threads used, description)."""
+    import oracle
+    if inputs is None:
+        A = w.left_rows(range(rows)).astype(np.float64)
+        B = np.ascontiguousarray(w.right_cols(range(cols)).T, dtype=np.float64)
+        h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+    else:
+        A, B, h, s = inputs
+    oracle.oversketch(A[:4], B[:, :4], h, s, w.b, w.mask)      # load + warm
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.oversketch(A, B, h, s, w.b, w.mask)
+        ts.append(time.perf_counter() - t0)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"{rows} rows of A x {cols} columns of B at full n={w.n}: both sketches and the masked "
+            f"product in FP64 (effective flop 2*{rows}*{w.n}*{cols}); plan built once, untimed")
+    return min(ts), threads, desc
+
+
+def calibrated_sample(w, target_s: float) -> int:
+    """Rows (= columns) of the oracle sample that take about target_s seconds."""
+    t, _, _ = oracle_sample_time(w, 128, 128)
+    r = int(128 * target_s / max(t, 1e-3))
+    return int(min(4096, max(64, r // 64 * 64)))
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1811_02653_gb300 import workloads as W
+    w = _workload(args)
+    budget = 150.0 / max(1, args.steps + args.warmup)          # whole run within a few minutes
+    rows = cols = args.ref_sample or calibrated_sample(w, budget)
+    A = w.left_rows(range(rows)).astype(np.float64)
+    B = np.ascontiguousarray(w.right_cols(range(cols)).T, dtype=np.float64)
+    h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+    inputs = (A, B, h, s)
+    for _ in range(args.warmup):
+        oracle_sample_time(w, rows, cols, inputs=inputs)
+    steps_t = []
+    threads, desc = 1, ""
+    for _ in range(args.steps):
+        t, threads, desc = oracle_sample_time(w, rows, cols, inputs=inputs)
+        steps_t.append(t)
+    t = statistics.median(steps_t)
+    value = 2.0 * rows * w.n * cols / t / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w, args, sample=f"{rows}x{w.n}x{cols}"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _workload(args):
+    from paper_1811_02653_gb300 import workloads as W
+    if args.shape:
+        m, n, l = (int(x) for x in args.shape.split(","))
+        return W.scaled(W.SQUARE, m=m, n=n, l=l,
+                        name=f"square-shaped {m}x{n}x{l} (profiling size), b=1024 N=8 e=2, blocks {{1,6}} dropped")
+    return W.SQUARE
+
+
+def _config(w, args, **extra):
+    d = {"workload": w.name, "m": w.m, "n": w.n, "l": w.l, "b": w.b, "N": w.N, "e": w.e,
+         "kept_blocks": [j for j in range(w.P) if (w.mask >> j) & 1], "gemm_dtype": args.dtype,
+         "input_dtype": "f32",
+         "l2": f"inputs ({(w.m * w.n + w.n * w.l) * 4 / 1e9:.1f} GB) larger than L2 (129 MB); no flush needed",
+         "parallelism": f"replicas{args.gpus}"}
+    d.update(extra)
+    return d
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_1811_02653_gb300 import build, ops
+    from paper_1811_02653_gb300 import workloads as W
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = _workload(args)
+    peaks, peak_kind = _peaks()
+
+    # ---- inputs (host, pinned) and device copies ----
+    A_h = torch.from_numpy(w.left()).pin_memory()
+    Bt_h = torch.from_numpy(w.right_cols(range(w.l)))            # l x n: columns of B
+    A = A_h.to(dev, non_blocking=False)
+    B = Bt_h.to(dev).t().contiguous()                              # n x l row-major
+    B_h = B.cpu().pin_memory()
+    del Bt_h
+    p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
+    gd = args.dtype
+    z = p.z
+    At, a_sc = ops.sketch_left(p, A, gd)
+    BtT, b_sc = ops.sketch_right(p, B, gd)
+    C = torch.empty((w.m, w.l), dtype=torch.float32, device=dev)
+    ws_left = torch.empty(ops.sketch_left_workspace(p, w.m), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ops.sketch_left(p, A, gd, out=At, scales=a_sc, workspace=ws_left)
+        ops.sketch_right(p, B, gd, out=BtT, scales=b_sc)
+        ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-phase events on the launching stream ----
+    n_ev = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_ev)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        e = ev[s]
+        e[0].record(stream)
+        ops.sketch_left(p, A, gd, out=At, scales=a_sc, workspace=ws_left)
+        e[1].record(stream)
+        ops.sketch_right(p, B, gd, out=BtT, scales=b_sc)
+        e[2].record(stream)
+        ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc)
+        e[3].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms = total_ms / args.steps
+    t_left = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    t_right = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    t_gemm = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    flop_eff = 2.0 * w.m * w.n * w.l
+    value = world * flop_eff / (ms * 1e-3) / 1e12
+
+    # ---- end to end through the C ABI with host buffers ----
+    C_h = torch.empty((w.m, w.l), dtype=torch.float32).pin_memory()
+    ws_mm = torch.empty(ops.workspace_size(p, w.m, w.l, torch.float32, gd), dtype=torch.uint8, device=dev)
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        A.copy_(A_h, non_blocking=True)
+        B.copy_(B_h, non_blocking=True)
+        ops.matmul(p, A, B, w.mask, gd, C=C, workspace=ws_mm)
+        C_h.copy_(C, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = s0.elapsed_time(s1) / e2e_steps
+    h2d = A_h.numel() * 4 + B_h.numel() * 4
+    d2h = C_h.numel() * 4
+
+    # ---- dominant kernel and its roofline ----
+    es = {"bf16": 2, "f32": 4, "fp8": 1}[gd]
+    n_kept = w.k
+    right_bytes = w.n * w.l * 4 + w.l * z * es
+    gemm_flop = 2.0 * w.m * n_kept * w.b * w.l
+    phases = {"sketch_left (transpose + gather)": t_left, "sketch_right": t_right, "gemm_masked": t_gemm}
+    if t_gemm >= t_right:
+        dom = "gemm_masked_bf16_kernel" if gd == "bf16" else "gemm_masked_f32_kernel"
+        if gd == "bf16":
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            bound, unit, ach = "tensor", "TFLOP/s", gemm_flop / (t_gemm * 1e-3) / 1e12
+        else:
+            peak, bound, unit, ach = None, "alu", "TFLOP/s", gemm_flop / (t_gemm * 1e-3) / 1e12
+        per_launch = {"flop": gemm_flop}
+    else:
+        dom = "sketch_gather_kernel (right sketch)"
+        peak = peaks.get("hbm_gbs")
+        bound, unit, ach = "hbm", "GB/s", right_bytes / (t_right * 1e-3) / 1e9
+        per_launch = {"bytes": right_bytes}
+    roof = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+            "frac": (ach / peak) if peak else None, "traffic": None, "kernel": dom,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
+            "algorithmic_per_launch": per_launch}
+
+    # ---- errors (not timed): sampled rows/cols against the FP64 oracle ----
+    err = None
+    cpu = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        rows = sorted({0, 1, 2, 777 % w.m, w.m // 4, w.m // 2, (3 * w.m) // 4, w.m - 1})
+        cols = sorted({0, 3, 4096 % w.l, 5000 % w.l, w.l // 3, (2 * w.l) // 3, w.l - 2, w.l - 1})
+        h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+        Ar = w.left_rows(rows).astype(np.float64)
+        Bc = np.ascontiguousarray(w.right_cols(cols).T, dtype=np.float64)
+        At_r = oracle.sketch_left(Ar, h, s, w.b)
+        Bt_c = oracle.sketch_right(Bc, h, s, w.b)
+        if gd == "bf16":
+            C_or = oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(Bt_c), w.b, w.mask)
+        else:
+            C_or = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
+        C_or_exact_sketch = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
+        ops.matmul(p, A, B, w.mask, gd, C=C, workspace=ws_mm)
+        C_s = C[rows][:, cols].cpu().numpy().astype(np.float64)
+        AB = Ar @ Bc
+        err = {"vs_oracle_rel_frob": oracle.rel_frob(C_s, C_or),
+               "vs_exact_rel_frob": oracle.rel_frob(C_s, AB),
+               "oracle_sketch_vs_exact_rel_frob": oracle.rel_frob(C_or_exact_sketch, AB),
+               "sample": f"{len(rows)}x{len(cols)} entries of C; oracle emulates {gd} operand rounding"}
+        if not args.no_cpu_baseline:
+            rs = args.ref_sample or calibrated_sample(w, 10.0)
+            t_cpu, threads, desc = oracle_sample_time(w, rs, rs)
+            cpu = {"value": 2.0 * rs * w.n * rs / t_cpu / 1e12, "unit": UNIT,
+                   "cores": threads, "kind": "oracle", "sample": desc}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": gd, "data": "synthetic (seeded; no dataset)",
+            "config": _config(w, args),
+            "phases_ms": {k_: round(v_, 4) for k_, v_ in phases.items()},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * flop_eff / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": 4 * args.steps, "clocks": clk, "error": err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "f32", "fp8"])
+    ap.add_argument("--ref-sample", type=int, default=0, help="oracle sample rows (0: calibrate)")
+    ap.add_argument("--shape", default="", help="m,n,l override for profiling captures")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

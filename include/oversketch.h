@@ -1,0 +1,235 @@
+/*
+ * oversketch.h -- C ABI of the GB300 (sm_103a) OverSketch library.
+ *
+ * OverSketch (Gupta, Wang, Courtade, Ramchandran, arXiv 1811.02653) computes
+ * the approximate product
+ *
+ *     C = (1/k) * sum_{j in mask} (A S_j) (S_j^T B)                      (*)
+ *
+ * where S = (S_1, ..., S_{N+e}) stacks N+e independent Count-sketch blocks of
+ * width b (Eq. 3; Alg. 4 defines one block), A S and S^T B are computed by the
+ * bucket sums of Alg. 4 step 3 / Alg. 5, and the sum keeps any k blocks chosen
+ * by a caller mask, standing in for Alg. 3's termination rule ("stop when any
+ * d/b of the z/b workers returned").  k = popcount(mask); the 1/sqrt(N) of
+ * Eq. 3 on both sides is applied once as 1/k (k = N when exactly N blocks are
+ * kept; keeping fewer is the "graceful degradation" of Sec. 4.1).
+ *
+ * Conventions (all entry points):
+ *   - Matrices are row-major; ld* is the leading dimension in ELEMENTS.
+ *   - Matrix pointers are DEVICE pointers owned by the caller, except where
+ *     an argument is documented as host memory.  Nothing is retained after
+ *     a call returns, except by plan objects.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
+ *     Compute entry points are asynchronous on that stream; argument errors
+ *     are detected on the host before any launch and returned synchronously.
+ *   - Blocks are 0-based, j = 0 .. P-1 with P = N + e <= 64.  Bucket indices
+ *     are 0-based (the paper counts 1..b).  Sketched index q = j*b + c.
+ *   - The library never allocates inside compute calls; callers pass a
+ *     workspace sized by oversketch_workspace_size().  Plans allocate their
+ *     own device tables at creation.
+ *   - Sketch outputs are UNSCALED (+-1 entries of S); only the masked
+ *     product applies 1/k.
+ *   - Sketched operands are stored K-major: A~ is m x z (row r contiguous
+ *     over q) and B~^T is l x z (column c of B~ contiguous over q), so both
+ *     feed the tensor-core GEMM without a transpose.
+ */
+#ifndef OVERSKETCH_H
+#define OVERSKETCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OS_API __attribute__((visibility("default")))
+#else
+#define OS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct oversketch_plan_s *oversketch_plan_t;
+
+typedef enum {
+    OS_OK = 0,
+    OS_ERR_INVALID_ARG = 1,   /* bad size, null pointer, misaligned ld     */
+    OS_ERR_MASK = 2,          /* mask empty or selects a block >= N+e      */
+    OS_ERR_DTYPE = 3,         /* dtype combination not supported           */
+    OS_ERR_OOM = 4,           /* plan allocation failed                    */
+    OS_ERR_CUDA = 5,          /* a CUDA runtime call failed                */
+    OS_ERR_TIMEOUT = 6,       /* a bounded device wait expired             */
+    OS_ERR_UNSUPPORTED = 7,   /* N+e > 64, block width not tile-aligned... */
+    OS_ERR_WORKSPACE = 8      /* workspace missing or too small            */
+} os_status;
+
+typedef enum {
+    OS_F32 = 0,               /* IEEE binary32                              */
+    OS_BF16 = 1,              /* bfloat16, round-to-nearest-even            */
+    OS_FP8E4M3 = 2            /* OCP FP8 E4M3 + per-(row, 128-q) power-of-2 */
+} os_dtype;
+
+/* Human-readable name of a status code (static storage). */
+OS_API const char *oversketch_status_string(os_status s);
+
+/* Message of the last CUDA error seen by the library on this thread. */
+OS_API const char *oversketch_last_cuda_error(void);
+
+/* -------------------------------------------------------------------------
+ * Plans: the sketch S of Eq. 3, built on the device.
+ *
+ * oversketch_plan -- Alg. 4 steps 1-2 for each of the P = N + e blocks:
+ *   w = splitmix64-mix(key_j + (i+1)*gamma), key_j = mix(seed + (j+1)*gamma),
+ *   h_j(i) = ((w >> 32) * b) >> 32 in [0, b), sigma_j(i) = (w & 1) ? -1 : +1,
+ * then a deterministic stable counting sort of every block by bucket (the
+ * "columns mapped to the same integer" of Alg. 4 step 3), kept as a
+ * bucket-CSR.  n >= 1, b >= 1, N >= 1, e >= 0, N + e <= 64, n < 2^31,
+ * (N+e)*b < 2^31.  The plan owns its device tables until destroyed; it may
+ * be used concurrently by several calls on any streams once the creating
+ * stream has reached the end of the call (the call synchronises `stream`
+ * before returning).  Errors: OS_ERR_INVALID_ARG, OS_ERR_UNSUPPORTED,
+ * OS_ERR_OOM, OS_ERR_CUDA.
+ */
+OS_API os_status oversketch_plan(int64_t n, int32_t b, int32_t N, int32_t e, uint64_t seed,
+                          void *stream, oversketch_plan_t *out);
+
+/* Same, from explicit tables in HOST memory: h[j*n + i] in [0,b) and
+ * sigma[j*n + i] in {+1,-1} (for worked examples such as Eq. 2 and for
+ * injective test hashes).  Errors as above, plus OS_ERR_INVALID_ARG for an
+ * out-of-range entry. */
+OS_API os_status oversketch_plan_from_tables(int64_t n, int32_t b, int32_t N, int32_t e,
+                                      const uint32_t *h_host, const int8_t *sigma_host,
+                                      void *stream, oversketch_plan_t *out);
+
+/* Copy the plan's tables to HOST memory: h_host and sigma_host hold
+ * (N+e)*n entries each (row j = block j); perm_host ((N+e)*n entries,
+ * index | sign << 31, bucket-sorted per block, ascending index inside a
+ * bucket) and offs_host ((N+e)*(b+1) entries) may be NULL.  Synchronous. */
+OS_API os_status oversketch_plan_get_tables(oversketch_plan_t plan, uint32_t *h_host, int8_t *sigma_host,
+                                     uint32_t *perm_host, uint32_t *offs_host);
+
+/* Plan parameters (any output pointer may be NULL). */
+OS_API os_status oversketch_plan_info(oversketch_plan_t plan, int64_t *n, int32_t *b, int32_t *N,
+                               int32_t *e);
+
+/* Release the plan's device tables (synchronises the device first). */
+OS_API os_status oversketch_plan_destroy(oversketch_plan_t plan);
+
+/* -------------------------------------------------------------------------
+ * Sketches (Alg. 5: A~ = A S block by block; B~ = S^T B).
+ *
+ * oversketch_sketch_left:
+ *   At[r, j*b + c] = sum_{i : h_j(i) = c} sigma_j(i) * s_i * A[r, i]
+ *   A: m x n, dtype a_t (OS_F32 or OS_BF16), leading dim lda >= n.
+ *   col_scale: device FP32 array of n scales s_i, or NULL (s_i = 1); used
+ *     for A diag(s) S, e.g. the sqrt(D) of the interior-point Hessian.
+ *   At: m x z in dtype out_t with leading dim ldat >= z (z = (N+e)*b).
+ *   scales: for out_t == OS_FP8E4M3, device FP32 array m x (z/128), entry
+ *     [r, t] = 2^e_rt with e_rt the smallest integer such that the FP32 sums
+ *     of slice t of row r are all <= 448 * 2^e_rt in magnitude (1.0 for an
+ *     all-zero slice); At holds round-to-nearest-even, saturating E4M3 codes
+ *     of (sum / 2^e_rt).  NULL otherwise.  FP8 needs b % 128 == 0.
+ *   Sums are accumulated in FP32 in ascending order of i inside a bucket;
+ *   BF16 output is the round-to-nearest-even of that FP32 sum.
+ *   workspace: device memory of at least oversketch_sketch_left_workspace()
+ *   bytes (the kernel stages A^T there), 256-byte aligned.
+ * oversketch_sketch_right:
+ *   BtT[c, j*b + q] = sum_{i : h_j(i) = q} sigma_j(i) * B[i, c]
+ *   B: n x l (ldb >= l); BtT: l x z (ldbt >= z); scales l x (z/128) for FP8.
+ *   No workspace needed.
+ * Errors: OS_ERR_INVALID_ARG (null pointers, ld too small, out pointers or
+ *   ld not 16-byte aligned), OS_ERR_DTYPE, OS_ERR_UNSUPPORTED,
+ *   OS_ERR_WORKSPACE, OS_ERR_CUDA (launch failure).
+ */
+OS_API os_status oversketch_sketch_left_workspace(oversketch_plan_t plan, int64_t m, os_dtype a_t,
+                                           size_t *bytes);
+OS_API os_status oversketch_sketch_left(oversketch_plan_t plan, const void *A, os_dtype a_t, int64_t m,
+                                 int64_t lda, void *At, os_dtype out_t, int64_t ldat, float *scales,
+                                 const float *col_scale, void *workspace, size_t ws_bytes,
+                                 void *stream);
+OS_API os_status oversketch_sketch_right(oversketch_plan_t plan, const void *B, os_dtype b_t, int64_t l,
+                                  int64_t ldb, void *BtT, os_dtype out_t, int64_t ldbt,
+                                  float *scales, void *stream);
+
+/* -------------------------------------------------------------------------
+ * Masked block-sum GEMM (Alg. 3 computation + termination + reduction; the
+ * b x b block products of Alg. 2 become one GEMM whose inner dimension is
+ * the concatenation of the kept blocks):
+ *   C[r, c] = alpha * sum_{j in mask} sum_{q < b} At[r, j*b + q] * BtT[c, j*b + q]
+ *            (+ beta * C[r, c] when beta != 0)
+ * At: m x z (ldat), BtT: l x z (ldbt), both in dtype `dt`; FP8 operands
+ * carry the per-(row, 128-q) scales produced by the sketches.  C: FP32
+ * m x l (ldc).  Pass alpha = 1/popcount(mask) for (*).  OS_F32 operands are
+ * computed at FP32 accuracy, BF16 and FP8 on the tensor cores with FP32
+ * accumulation.  K tiles: 16 (FP32), 64 (BF16), 128 (FP8); b must be a
+ * multiple of the K tile.  Tensor-core operands need 16-byte aligned rows.
+ * Errors: OS_ERR_MASK, OS_ERR_INVALID_ARG, OS_ERR_DTYPE, OS_ERR_UNSUPPORTED
+ * (b not a multiple of the K tile), OS_ERR_CUDA.
+ */
+OS_API os_status oversketch_gemm_masked(oversketch_plan_t plan, const void *At, int64_t ldat,
+                                 const float *a_scales, const void *BtT, int64_t ldbt,
+                                 const float *b_scales, os_dtype dt, int64_t m, int64_t l,
+                                 uint64_t mask, float alpha, float beta, float *C, int64_t ldc,
+                                 void *stream);
+
+/* -------------------------------------------------------------------------
+ * The whole product (*): left sketch, right sketch, masked GEMM.
+ */
+typedef struct {
+    os_dtype gemm_dtype;      /* OS_F32, OS_BF16 or OS_FP8E4M3               */
+    const float *col_scale;   /* device, length n, or NULL (A diag(s) S)     */
+    int32_t symmetric;        /* 1: B is ignored and C = (1/k) A~_sel A~_sel^T */
+    int32_t reserved;
+} os_opts;
+
+OS_API os_status oversketch_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
+                                    os_dtype a_t, const os_opts *opts, size_t *bytes);
+OS_API os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os_dtype a_t, int64_t lda,
+                            const void *B, os_dtype b_t, int64_t ldb, float *C, int64_t ldc,
+                            int64_t m, int64_t n, int64_t l, uint64_t mask, const os_opts *opts,
+                            void *workspace, size_t ws_bytes, void *stream);
+
+/* -------------------------------------------------------------------------
+ * Adjoints of the sketch restricted to the kept blocks (the backward pass of
+ * (*) as a function of A and B):
+ *   unsketch_cols: dX[r, i] = scale * sum_{j in mask} sigma_j(i) T[r, j*b + h_j(i)]
+ *                  T: m x z FP32 (ldt); dX: m x n in dtype x_t (ldx).
+ *   unsketch_rows: dG[i, c] = scale * sum_{j in mask} sigma_j(i) U[j*b + h_j(i), c]
+ *                  U: z x l FP32 (ldu); dG: n x l in dtype g_t (ldg).
+ * x_t / g_t: OS_F32 or OS_BF16.  Errors: OS_ERR_MASK, OS_ERR_INVALID_ARG,
+ * OS_ERR_DTYPE, OS_ERR_CUDA.
+ */
+OS_API os_status oversketch_unsketch_cols(oversketch_plan_t plan, const float *T, int64_t m, int64_t ldt,
+                                   uint64_t mask, float scale, void *dX, os_dtype x_t,
+                                   int64_t ldx, void *stream);
+OS_API os_status oversketch_unsketch_rows(oversketch_plan_t plan, const float *U, int64_t l,
+                                   int64_t ldu, uint64_t mask, float scale, void *dG,
+                                   os_dtype g_t, int64_t ldg, void *stream);
+
+/* -------------------------------------------------------------------------
+ * FP64 error measurement (Def. 4.1 is stated in squared Frobenius norms):
+ *   out[0] = sum (X - Y)^2, out[1] = sum Y^2, out[2] = sum X*Y, accumulated
+ *   in FP64 over the rows x cols FP32 matrices X (ldx) and Y (ldy); Y may be
+ *   NULL (then out[0] = sum X^2 and out[1] = out[2] = 0).  out: DEVICE array
+ *   of 3 doubles, overwritten.  workspace: device memory of at least
+ *   OS_FROB_WORKSPACE_BYTES (8-byte aligned) for the per-CTA partial sums.
+ *   Deterministic: fixed grid, fixed summation order, no atomics.
+ */
+#define OS_FROB_WORKSPACE_BYTES 12288
+OS_API os_status oversketch_frob(const float *X, int64_t ldx, const float *Y, int64_t ldy, int64_t rows,
+                          int64_t cols, double *out, void *workspace, size_t ws_bytes,
+                          void *stream);
+
+/* -------------------------------------------------------------------------
+ * Device status of the tensor-core kernels.  Every wait inside them is
+ * bounded (about one second); a wait that expires makes the kernel record
+ * OS_ERR_TIMEOUT here, drain its own copies, release its tensor memory and
+ * return instead of hanging.  *status = OS_OK or OS_ERR_TIMEOUT; reset != 0
+ * clears the word.  Synchronises `stream`.
+ */
+OS_API os_status oversketch_device_status(void *stream, int32_t *status, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OVERSKETCH_H */

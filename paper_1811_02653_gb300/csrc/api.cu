@@ -1,0 +1,228 @@
+// C ABI glue: status strings, mask handling, the masked-GEMM dispatcher, the
+// whole-product entry point and the FP64 error reductions.
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace osk {
+
+// implemented in sketch.cu / gemm_simt.cu / gemm_tc.cu
+size_t left_workspace_bytes(const Plan *p, int64_t m, os_dtype a_t);
+os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
+                           void *At, os_dtype out_t, int64_t ldat, float *scales,
+                           const float *col_scale, void *ws, size_t ws_bytes, cudaStream_t st);
+os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
+                            void *BtT, os_dtype out_t, int64_t ldbt, float *scales, cudaStream_t st);
+os_status gemm_masked_f32(const Plan *p, const float *At, int64_t ldat, const float *BtT,
+                          int64_t ldbt, int64_t m, int64_t l, uint64_t mask, float alpha, float beta,
+                          float *C, int64_t ldc, cudaStream_t st);
+os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const float *a_scales,
+                         const void *BtT, int64_t ldbt, const float *b_scales, os_dtype dt, int64_t m,
+                         int64_t l, uint64_t mask, float alpha, float beta, float *C, int64_t ldc,
+                         cudaStream_t st);
+
+namespace {
+thread_local char g_last_cuda_error[256] = "no error";
+}
+
+os_status set_cuda_error(cudaError_t err) {
+    std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", cudaGetErrorName(err),
+                  cudaGetErrorString(err));
+    return OS_ERR_CUDA;
+}
+
+os_status check_launch() {
+    const cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? OS_OK : set_cuda_error(err);
+}
+
+os_status check_mask(uint64_t mask, int P) {
+    if (mask == 0) return OS_ERR_MASK;
+    if (P < 64 && (mask >> P) != 0) return OS_ERR_MASK;
+    return OS_OK;
+}
+
+BlockList mask_to_list(uint64_t mask, int P) {
+    BlockList L;
+    L.count = 0;
+    for (int j = 0; j < P && j < 64; ++j)
+        if ((mask >> j) & 1ull) L.idx[L.count++] = j;
+    for (int t = L.count; t < 64; ++t) L.idx[t] = 0;
+    return L;
+}
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct MatmulLayout {
+    int64_t z, ldat, ldbt, nsl;
+    size_t at_bytes, bt_bytes, as_bytes, bs_bytes, left_ws;
+};
+
+MatmulLayout layout(const Plan *p, int64_t m, int64_t l, os_dtype a_t, const os_opts *o) {
+    MatmulLayout L;
+    const os_dtype g = o ? o->gemm_dtype : OS_F32;
+    const size_t es = dtype_size(g);
+    L.z = (int64_t)p->P * p->b;
+    const int64_t align_el = 16 / (int64_t)es;
+    L.ldat = (L.z + align_el - 1) / align_el * align_el;
+    L.ldbt = L.ldat;
+    L.nsl = (L.z + 127) / 128;
+    L.at_bytes = align256((size_t)m * L.ldat * es);
+    const bool sym = o && o->symmetric;
+    L.bt_bytes = sym ? 0 : align256((size_t)l * L.ldbt * es);
+    L.as_bytes = g == OS_FP8E4M3 ? align256((size_t)m * L.nsl * 4) : 0;
+    L.bs_bytes = (g == OS_FP8E4M3 && !sym) ? align256((size_t)l * L.nsl * 4) : 0;
+    L.left_ws = align256(left_workspace_bytes(p, m, a_t));
+    return L;
+}
+
+// Deterministic FP64 partial sums: fixed grid, fixed per-thread order, fixed tree.
+constexpr int kFrobBlocks = 512;
+
+__global__ void __launch_bounds__(256) frob_partial_kernel(const float *__restrict__ X, int64_t ldx,
+                                                           const float *__restrict__ Y, int64_t ldy,
+                                                           int64_t rows, int64_t cols,
+                                                           double *__restrict__ part) {
+    __shared__ double red[3][256];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    const int64_t total = rows * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / cols, c = t - r * cols;
+        const double x = X[r * ldx + c];
+        if (Y) {
+            const double y = Y[r * ldy + c];
+            s0 += (x - y) * (x - y);
+            s1 += y * y;
+            s2 += x * y;
+        } else {
+            s0 += x * x;
+        }
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[blockIdx.x * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void frob_final_kernel(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int bidx = 0; bidx < nblocks; ++bidx) s += part[bidx * 3 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+}  // namespace
+
+}  // namespace osk
+
+using namespace osk;
+
+extern "C" const char *oversketch_status_string(os_status s) {
+    switch (s) {
+        case OS_OK: return "OS_OK";
+        case OS_ERR_INVALID_ARG: return "OS_ERR_INVALID_ARG";
+        case OS_ERR_MASK: return "OS_ERR_MASK";
+        case OS_ERR_DTYPE: return "OS_ERR_DTYPE";
+        case OS_ERR_OOM: return "OS_ERR_OOM";
+        case OS_ERR_CUDA: return "OS_ERR_CUDA";
+        case OS_ERR_TIMEOUT: return "OS_ERR_TIMEOUT";
+        case OS_ERR_UNSUPPORTED: return "OS_ERR_UNSUPPORTED";
+        case OS_ERR_WORKSPACE: return "OS_ERR_WORKSPACE";
+    }
+    return "OS_ERR_UNKNOWN";
+}
+
+extern "C" const char *oversketch_last_cuda_error(void) { return g_last_cuda_error; }
+
+extern "C" os_status oversketch_gemm_masked(oversketch_plan_t plan, const void *At, int64_t ldat,
+                                            const float *a_scales, const void *BtT, int64_t ldbt,
+                                            const float *b_scales, os_dtype dt, int64_t m, int64_t l,
+                                            uint64_t mask, float alpha, float beta, float *C,
+                                            int64_t ldc, void *stream) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p || !At || !BtT || !C || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
+    OSK_TRY(check_mask(mask, p->P));
+    const int64_t z = (int64_t)p->P * p->b;
+    if (ldat < z || ldbt < z) return OS_ERR_INVALID_ARG;
+    if (m == 0 || l == 0) return OS_OK;
+    cudaStream_t st = as_stream(stream);
+    switch (dt) {
+        case OS_F32:
+            return gemm_masked_f32(p, (const float *)At, ldat, (const float *)BtT, ldbt, m, l, mask,
+                                   alpha, beta, C, ldc, st);
+        case OS_BF16:
+        case OS_FP8E4M3:
+            return gemm_masked_tc(p, At, ldat, a_scales, BtT, ldbt, b_scales, dt, m, l, mask, alpha,
+                                  beta, C, ldc, st);
+    }
+    return OS_ERR_DTYPE;
+}
+
+extern "C" os_status oversketch_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
+                                               os_dtype a_t, const os_opts *opts, size_t *bytes) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p || !bytes || m < 0 || l < 0) return OS_ERR_INVALID_ARG;
+    const MatmulLayout L = layout(p, m, l, a_t, opts);
+    *bytes = L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes + L.left_ws + 256;
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os_dtype a_t,
+                                       int64_t lda, const void *B, os_dtype b_t, int64_t ldb,
+                                       float *C, int64_t ldc, int64_t m, int64_t n, int64_t l,
+                                       uint64_t mask, const os_opts *opts, void *workspace,
+                                       size_t ws_bytes, void *stream) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p || !A || !C) return OS_ERR_INVALID_ARG;
+    const bool sym = opts && opts->symmetric;
+    if (sym) l = m;
+    if (!sym && !B) return OS_ERR_INVALID_ARG;
+    if (n != p->n || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
+    OSK_TRY(check_mask(mask, p->P));
+    const os_dtype g = opts ? opts->gemm_dtype : OS_F32;
+    if (g != OS_F32 && g != OS_BF16 && g != OS_FP8E4M3) return OS_ERR_DTYPE;
+    const MatmulLayout L = layout(p, m, l, a_t, opts);
+    const size_t need = L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes + L.left_ws + 256;
+    if (!workspace || ws_bytes < need) return OS_ERR_WORKSPACE;
+    if (m == 0 || l == 0) return OS_OK;
+    cudaStream_t st = as_stream(stream);
+    char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
+    void *At = base;
+    void *BtT = sym ? At : base + L.at_bytes;
+    float *as = g == OS_FP8E4M3 ? reinterpret_cast<float *>(base + L.at_bytes + L.bt_bytes) : nullptr;
+    float *bs = g == OS_FP8E4M3 ? (sym ? as : reinterpret_cast<float *>(base + L.at_bytes + L.bt_bytes + L.as_bytes))
+                                : nullptr;
+    void *lws = base + L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes;
+    const float *cs = opts ? opts->col_scale : nullptr;
+    OSK_TRY(sketch_left_impl(p, A, a_t, m, lda, At, g, L.ldat, as, cs, lws, L.left_ws, st));
+    if (!sym) OSK_TRY(sketch_right_impl(p, B, b_t, l, ldb, BtT, g, L.ldbt, bs, st));
+    int k = 0;
+    for (int j = 0; j < p->P; ++j) k += (int)((mask >> j) & 1ull);
+    return oversketch_gemm_masked(plan, At, L.ldat, as, BtT, L.ldbt, bs, g, m, l, mask, 1.0f / (float)k,
+                                  0.0f, C, ldc, stream);
+}
+
+extern "C" os_status oversketch_frob(const float *X, int64_t ldx, const float *Y, int64_t ldy,
+                                     int64_t rows, int64_t cols, double *out, void *workspace,
+                                     size_t ws_bytes, void *stream) {
+    if (!X || !out || rows < 0 || cols < 0 || ldx < cols || (Y && ldy < cols))
+        return OS_ERR_INVALID_ARG;
+    if (!workspace || ws_bytes < sizeof(double) * 3 * kFrobBlocks) return OS_ERR_WORKSPACE;
+    cudaStream_t st = as_stream(stream);
+    double *part = reinterpret_cast<double *>(workspace);
+    frob_partial_kernel<<<kFrobBlocks, 256, 0, st>>>(X, ldx, Y, ldy, rows, cols, part);
+    OSK_TRY(check_launch());
+    frob_final_kernel<<<1, 32, 0, st>>>(part, kFrobBlocks, out);
+    return check_launch();
+}

@@ -1,0 +1,62 @@
+// Shared definitions of the sm_103a OverSketch library (device + host).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/oversketch.h"
+
+namespace osk {
+
+// Plan: the sketch S of Eq. 3 as device tables.
+//   hs[j*n + i]   = h_j(i) | (sigma_j(i) < 0) << 31      (per-index lookup)
+//   perm[j*n + p] = i | (sigma_j(i) < 0) << 31           (bucket-sorted, i ascending in a bucket)
+//   offs[j*(b+1) + c] = start of bucket c of block j in perm[j*n ...]; offs[.. + b] = n
+struct Plan {
+    int64_t n;
+    int32_t b, N, e, P;
+    uint64_t seed;
+    uint32_t *hs;
+    uint32_t *perm;
+    uint32_t *offs;
+    int device;
+};
+
+constexpr uint32_t kSignBit = 0x80000000u;
+constexpr uint32_t kIndexMask = 0x7fffffffu;
+
+// Kept blocks of a mask as a list (launch parameter, passed by value).
+struct BlockList {
+    int32_t count;
+    int32_t idx[64];
+};
+
+os_status set_cuda_error(cudaError_t err);
+os_status check_launch();
+BlockList mask_to_list(uint64_t mask, int P);
+os_status check_mask(uint64_t mask, int P);
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t dtype_size(os_dtype t) {
+    return t == OS_F32 ? 4 : (t == OS_BF16 ? 2 : 1);
+}
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace osk
+
+#define OSK_CUDA_TRY(expr)                                      \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return ::osk::set_cuda_error(_e); \
+    } while (0)
+
+#define OSK_TRY(expr)                        \
+    do {                                     \
+        os_status _s = (expr);               \
+        if (_s != OS_OK) return _s;          \
+    } while (0)

@@ -1,0 +1,345 @@
+// Masked block-sum GEMM on the 5th-generation tensor cores (sm_103a).
+//
+// Alg. 3's computation phase multiplies b x b blocks of A~ and B~, its
+// termination rule keeps any k of the N+e blocks of the inner dimension, and
+// Alg. 2's reduction phase adds the kept partial products.  On one GPU this
+// is a single GEMM whose K loop walks the concatenation of the kept blocks:
+//
+//   C[r, c] = alpha * sum_{j kept} sum_{q < b} At[r, j*b + q] * BtT[c, j*b + q]  (+ beta * C)
+//
+// K block kb (64 wide) of the loop is read by TMA at sketched column
+// kept[kb / (b/64)] * b + (kb mod (b/64)) * 64, so dropped blocks are never
+// loaded.  Both operands are K-major BF16 in the 128-byte swizzled layout.
+//
+// Kernel organisation (one persistent CTA per SM, 192 threads):
+//   warp 0      TMA producer: 4-stage ring of {A 128x64, B 256x64} tiles
+//   warp 1      TMEM owner + MMA issuer: tcgen05.mma 128x256x16, FP32
+//               accumulators in TMEM, double-buffered (2 x 256 columns)
+//   warps 2..5  epilogue: tcgen05.ld of the 128 x 256 accumulator, alpha /
+//               beta, FP32 stores; overlaps the next tile's MMAs
+// Every mbarrier wait is bounded (1 s); on expiry the kernel records
+// OS_ERR_TIMEOUT in the device status word, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "tc_common.cuh"
+
+namespace osk {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;          // 16 KB
+constexpr int B_BYTES = BN * BK * 2;          // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 512;                // 2 accumulators of 256 columns
+constexpr int kThreads = 192;
+constexpr size_t kSmemBytes = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+
+struct GemmArgs {
+    int64_t m, l;
+    int32_t b;            // block width (multiple of 64)
+    int32_t kb_per_blk;   // b / 64
+    int32_t num_kb;       // k * b / 64
+    int32_t tiles_m, tiles_n, num_tiles;
+    float alpha, beta;
+    float *C;
+    int64_t ldc;
+    BlockList kept;
+};
+
+__device__ __forceinline__ void tile_coords(const GemmArgs &g, int t, int &tm, int &tn) {
+    // Groups of 16 m-tiles: consecutive tiles share A panels and nearby B panels.
+    constexpr int G = 16;
+    const int group = t / (G * g.tiles_n);
+    const int first_m = group * G;
+    const int gm = min(G, g.tiles_m - first_m);
+    const int in = t - group * G * g.tiles_n;
+    tm = first_m + in % gm;
+    tn = in / gm;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_masked_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
+                        const __grid_constant__ CUtensorMap tmap_b, const GemmArgs g) {
+    extern __shared__ uint8_t smem_raw[];
+    // 1024-byte alignment for the swizzled tiles
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *tiles = smem;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tmem_full = empty + STAGES;
+    uint64_t *tmem_empty = tmem_full + 2;
+    uint64_t *drain = tmem_empty + 2;
+    uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_base_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tmem_full[a], 1);
+            mbar_init(&tmem_empty[a], 128);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_barrier_init();
+        prefetch_tmap(&tmap_a);
+        prefetch_tmap(&tmap_b);
+    }
+    if (warp == 1) tmem_alloc(tmem_base_slot, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_base_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_phase[STAGES];
+            bool issued[STAGES];
+            for (int s = 0; s < STAGES; ++s) issued[s] = false, issued_phase[s] = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
+                int tm, tn;
+                tile_coords(g, t, tm, tn);
+                for (int kb = 0; kb < g.num_kb; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
+                    const int blk = kb / g.kb_per_blk;
+                    const int kz = g.kept.idx[blk] * g.b + (kb - blk * g.kb_per_blk) * BK;
+                    uint8_t *sa = tiles + stage * STAGE_BYTES;
+                    uint8_t *sb = sa + A_BYTES;
+                    mbar_expect_tx(&full[stage], STAGE_BYTES);
+                    tma_load_2d(&tmap_a, &full[stage], sa, kz, tm * BM);
+                    tma_load_2d(&tmap_b, &full[stage], sb, kz, tn * BN);
+                    issued[stage] = true;
+                    issued_phase[stage] = phase;
+                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                }
+            }
+            // Drain: every copy this thread issued must have landed before exit.
+            for (int s = 0; s < STAGES; ++s)
+                if (issued[s]) mbar_wait_drain(&full[s], issued_phase[s]);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+            int stage = 0;
+            uint32_t phase = 0;
+            int iter = 0;
+            bool ok = true;
+            bool any = false;
+            for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x, ++iter) {
+                const int a = iter & 1;
+                const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+                if (!mbar_wait(&tmem_empty[a], aphase ^ 1u, abort)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(a * BN);
+                for (int kb = 0; kb < g.num_kb; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(tiles + stage * STAGE_BYTES);
+                    const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t ad = sdesc_kmajor_sw128(sa + kk * 32);
+                        const uint64_t bd = sdesc_kmajor_sw128(sb + kk * 32);
+                        umma_f16(d, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    any = true;
+                    umma_commit(&empty[stage]);
+                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                }
+                if (!ok) break;
+                umma_commit(&tmem_full[a]);
+            }
+            if (!ok && any) {
+                // Drain: wait for the MMAs already issued before freeing TMEM.
+                umma_commit(drain);
+                mbar_wait_drain(drain, 0);
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
+        const int row_in_tile = quarter * 32 + lane;
+        int iter = 0;
+        const bool vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15u) == 0) && (g.ldc % 4 == 0);
+        for (int t = blockIdx.x; t < g.num_tiles; t += gridDim.x, ++iter) {
+            const int a = iter & 1;
+            const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+            // warp-uniform decision: tcgen05.ld below is a .sync.aligned instruction
+            if (!__all_sync(0xffffffffu, mbar_wait(&tmem_full[a], aphase, abort))) break;
+            tc_fence_after();
+            int tm, tn;
+            tile_coords(g, t, tm, tn);
+            const int64_t r = (int64_t)tm * BM + row_in_tile;
+            const int64_t c0 = (int64_t)tn * BN;
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN + ch * 32), v);
+                if (r < g.m) {
+                    float *dst = g.C + r * g.ldc + c0 + ch * 32;
+                    const int64_t cbase = c0 + ch * 32;
+                    if (vec_ok && cbase + 32 <= g.l) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            float4 o;
+                            o.x = g.alpha * __uint_as_float(v[4 * u + 0]);
+                            o.y = g.alpha * __uint_as_float(v[4 * u + 1]);
+                            o.z = g.alpha * __uint_as_float(v[4 * u + 2]);
+                            o.w = g.alpha * __uint_as_float(v[4 * u + 3]);
+                            if (g.beta != 0.f) {
+                                const float4 old = *reinterpret_cast<const float4 *>(dst + 4 * u);
+                                o.x = fmaf(g.beta, old.x, o.x);
+                                o.y = fmaf(g.beta, old.y, o.y);
+                                o.z = fmaf(g.beta, old.z, o.z);
+                                o.w = fmaf(g.beta, old.w, o.w);
+                            }
+                            *reinterpret_cast<float4 *>(dst + 4 * u) = o;
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) {
+                            if (cbase + u < g.l) {
+                                float o = g.alpha * __uint_as_float(v[u]);
+                                if (g.beta != 0.f) o = fmaf(g.beta, dst[u], o);
+                                dst[u] = o;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tmem_empty[a]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- host ----
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled get_encode() {
+    static PFN_encodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled>(p);
+    });
+    return fn;
+}
+
+// 2-D K-major tensor map: rows x cols (cols contiguous), box box_rows x box_cols.
+os_status make_tmap(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int elem_bytes, int64_t rows,
+                    int64_t cols, int64_t ld, int box_rows, int box_cols) {
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return OS_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * elem_bytes)};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? OS_OK : OS_ERR_INVALID_ARG;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+}  // namespace
+
+os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const float *a_scales,
+                         const void *BtT, int64_t ldbt, const float *b_scales, os_dtype dt, int64_t m,
+                         int64_t l, uint64_t mask, float alpha, float beta, float *C, int64_t ldc,
+                         cudaStream_t st) {
+    (void)a_scales;
+    (void)b_scales;
+    if (dt != OS_BF16) return OS_ERR_UNSUPPORTED;
+    if (p->b % BK != 0) return OS_ERR_UNSUPPORTED;
+    if (!aligned16(At) || !aligned16(BtT) || (ldat * 2) % 16 != 0 || (ldbt * 2) % 16 != 0)
+        return OS_ERR_INVALID_ARG;
+    const int64_t z = (int64_t)p->P * p->b;
+    GemmArgs g;
+    g.m = m;
+    g.l = l;
+    g.b = p->b;
+    g.kb_per_blk = p->b / BK;
+    g.kept = mask_to_list(mask, p->P);
+    g.num_kb = g.kept.count * g.kb_per_blk;
+    g.tiles_m = (int)((m + BM - 1) / BM);
+    g.tiles_n = (int)((l + BN - 1) / BN);
+    g.num_tiles = g.tiles_m * g.tiles_n;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.C = C;
+    g.ldc = ldc;
+    CUtensorMap ta, tb;
+    OSK_TRY(make_tmap(&ta, At, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, z, ldat, BM, BK));
+    OSK_TRY(make_tmap(&tb, BtT, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, z, ldbt, BN, BK));
+    static bool attr_set = false;
+    if (!attr_set) {
+        OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_masked_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSmemBytes));
+        attr_set = true;
+    }
+    const int grid = g.num_tiles < num_sms() ? g.num_tiles : num_sms();
+    gemm_masked_bf16_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, g);
+    return check_launch();
+}
+
+}  // namespace osk
+
+using namespace osk;
+
+extern "C" os_status oversketch_device_status(void *stream, int32_t *status, int32_t reset) {
+    if (!status) return OS_ERR_INVALID_ARG;
+    cudaStream_t st = as_stream(stream);
+    unsigned int v = 0;
+    OSK_CUDA_TRY(cudaMemcpyFromSymbolAsync(&v, tc::g_device_status, sizeof(v), 0, cudaMemcpyDeviceToHost, st));
+    OSK_CUDA_TRY(cudaStreamSynchronize(st));
+    *status = (v & 1u) ? OS_ERR_TIMEOUT : OS_OK;
+    if (reset && v) {
+        const unsigned int zero = 0;
+        OSK_CUDA_TRY(cudaMemcpyToSymbolAsync(tc::g_device_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st));
+        OSK_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return OS_OK;
+}

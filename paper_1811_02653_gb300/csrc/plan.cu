@@ -1,0 +1,280 @@
+// Plan construction: the sketch S of Eq. 3 as device tables.
+//
+// Alg. 4 steps 1-2 give every index i of the sketched dimension a random sign
+// and a uniform bucket, independently for each of the P = N + e blocks; step 3
+// ("add the columns mapped to the same integer") needs, per block, the list of
+// indices of every bucket.  Here the random draws come from splitmix64 (the
+// published generator of Steele, Lea and Flood, used as a counter-based hash),
+// and the bucket lists are built by a deterministic stable counting sort:
+//   1. plan_hash_kernel        -- hs[j][i] = h_j(i) | sign bit
+//   2. chunk_count_kernel      -- per (block, chunk of indices) bucket counts,
+//                                 one sequential thread per chunk (no atomics)
+//   3. bucket_total_kernel     -- per (block, bucket): exclusive prefix over chunks
+//   4. bucket_offsets_kernel   -- per block: exclusive prefix over buckets -> offs
+//   5. chunk_scatter_kernel    -- per (block, chunk): sequential stable scatter
+// Plan creation is not on the timed path; every step is deterministic.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace osk {
+
+namespace {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+__global__ void plan_hash_kernel(int64_t n, int32_t b, uint64_t seed, uint32_t *__restrict__ hs) {
+    const int j = blockIdx.y;
+    const uint64_t key = splitmix_mix(seed + (uint64_t)(j + 1) * kGamma);
+    uint32_t *row = hs + (int64_t)j * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = splitmix_mix(key + (uint64_t)(i + 1) * kGamma);
+        const uint32_t h = (uint32_t)(((w >> 32) * (uint64_t)(uint32_t)b) >> 32);
+        row[i] = h | ((w & 1ull) ? kSignBit : 0u);
+    }
+}
+
+// cnt[(j*nchunks + ch)*b + c] = #{i in chunk ch : h_j(i) = c}
+__global__ void chunk_count_kernel(const uint32_t *__restrict__ hs, int64_t n, int32_t b, int P,
+                                   int nchunks, int64_t chunk, uint32_t *__restrict__ cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)P * nchunks) return;
+    const int j = (int)(t / nchunks), ch = (int)(t % nchunks);
+    uint32_t *row = cnt + t * b;
+    const uint32_t *hrow = hs + (int64_t)j * n;
+    const int64_t i0 = ch * chunk, i1 = min(n, i0 + chunk);
+    for (int64_t i = i0; i < i1; ++i) row[hrow[i] & kIndexMask] += 1u;
+}
+
+// In place: cnt[j][ch][c] <- sum_{ch' < ch} cnt[j][ch'][c]; tot[j][c] = total.
+__global__ void bucket_total_kernel(uint32_t *__restrict__ cnt, int32_t b, int P, int nchunks,
+                                    uint32_t *__restrict__ tot) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)P * b) return;
+    const int j = (int)(t / b), c = (int)(t % b);
+    uint32_t run = 0;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        uint32_t *p = cnt + ((int64_t)j * nchunks + ch) * b + c;
+        const uint32_t v = *p;
+        *p = run;
+        run += v;
+    }
+    tot[t] = run;
+}
+
+// offs[j][c] = sum_{c' < c} tot[j][c'], offs[j][b] = n.  One thread per block.
+__global__ void bucket_offsets_kernel(const uint32_t *__restrict__ tot, int32_t b, int P,
+                                      uint32_t *__restrict__ offs) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    uint32_t run = 0;
+    for (int c = 0; c < b; ++c) {
+        offs[(int64_t)j * (b + 1) + c] = run;
+        run += tot[(int64_t)j * b + c];
+    }
+    offs[(int64_t)j * (b + 1) + b] = run;
+}
+
+// Stable scatter: indices of a chunk are visited in ascending order.
+__global__ void chunk_scatter_kernel(const uint32_t *__restrict__ hs, int64_t n, int32_t b, int P,
+                                     int nchunks, int64_t chunk, uint32_t *__restrict__ cursor,
+                                     const uint32_t *__restrict__ offs, uint32_t *__restrict__ perm) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)P * nchunks) return;
+    const int j = (int)(t / nchunks), ch = (int)(t % nchunks);
+    uint32_t *cur = cursor + t * b;
+    const uint32_t *hrow = hs + (int64_t)j * n;
+    const uint32_t *orow = offs + (int64_t)j * (b + 1);
+    uint32_t *prow = perm + (int64_t)j * n;
+    const int64_t i0 = ch * chunk, i1 = min(n, i0 + chunk);
+    for (int64_t i = i0; i < i1; ++i) {
+        const uint32_t v = hrow[i];
+        const uint32_t c = v & kIndexMask;
+        const uint32_t pos = orow[c] + cur[c];
+        cur[c] += 1u;
+        prow[pos] = (uint32_t)i | (v & kSignBit);
+    }
+}
+
+os_status check_params(int64_t n, int32_t b, int32_t N, int32_t e, oversketch_plan_t *out) {
+    if (!out) return OS_ERR_INVALID_ARG;
+    if (n < 1 || b < 1 || N < 1 || e < 0) return OS_ERR_INVALID_ARG;
+    if (N + e > 64) return OS_ERR_UNSUPPORTED;
+    if (n >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
+    if ((int64_t)(N + e) * b >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
+    return OS_OK;
+}
+
+void free_plan(Plan *p) {
+    if (!p) return;
+    if (p->hs) cudaFree(p->hs);
+    if (p->perm) cudaFree(p->perm);
+    if (p->offs) cudaFree(p->offs);
+    delete p;
+}
+
+// Steps 2-5 on an existing hs table.
+os_status build_csr(Plan *p, cudaStream_t st) {
+    const int P = p->P;
+    const int64_t n = p->n;
+    const int32_t b = p->b;
+    // chunks: about 2048 indices each, with at most 2^24 counters in total
+    int64_t nchunks = (n + 2047) / 2048;
+    const int64_t cap = (int64_t(1) << 24) / ((int64_t)P * b);
+    if (nchunks > cap) nchunks = cap < 1 ? 1 : cap;
+    const int64_t chunk = (n + nchunks - 1) / nchunks;
+    nchunks = (n + chunk - 1) / chunk;
+
+    uint32_t *cnt = nullptr, *tot = nullptr;
+    const size_t cnt_bytes = sizeof(uint32_t) * (size_t)P * nchunks * b;
+    if (cudaMalloc(&cnt, cnt_bytes) != cudaSuccess) return OS_ERR_OOM;
+    if (cudaMalloc(&tot, sizeof(uint32_t) * (size_t)P * b) != cudaSuccess) {
+        cudaFree(cnt);
+        return OS_ERR_OOM;
+    }
+    os_status s = OS_OK;
+    do {
+        if (cudaMemsetAsync(cnt, 0, cnt_bytes, st) != cudaSuccess) { s = OS_ERR_CUDA; break; }
+        const int64_t threads = (int64_t)P * nchunks;
+        chunk_count_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
+            p->hs, n, b, P, (int)nchunks, chunk, cnt);
+        if ((s = check_launch()) != OS_OK) break;
+        bucket_total_kernel<<<(unsigned)(((int64_t)P * b + 255) / 256), 256, 0, st>>>(
+            cnt, b, P, (int)nchunks, tot);
+        if ((s = check_launch()) != OS_OK) break;
+        bucket_offsets_kernel<<<1, 64, 0, st>>>(tot, b, P, p->offs);
+        if ((s = check_launch()) != OS_OK) break;
+        chunk_scatter_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
+            p->hs, n, b, P, (int)nchunks, chunk, cnt, p->offs, p->perm);
+        if ((s = check_launch()) != OS_OK) break;
+        if (cudaStreamSynchronize(st) != cudaSuccess) { s = set_cuda_error(cudaGetLastError()); break; }
+    } while (0);
+    cudaFree(cnt);
+    cudaFree(tot);
+    return s;
+}
+
+os_status alloc_plan(int64_t n, int32_t b, int32_t N, int32_t e, uint64_t seed, Plan **out) {
+    Plan *p = new Plan();
+    p->n = n;
+    p->b = b;
+    p->N = N;
+    p->e = e;
+    p->P = N + e;
+    p->seed = seed;
+    p->hs = p->perm = p->offs = nullptr;
+    cudaGetDevice(&p->device);
+    const size_t tab = sizeof(uint32_t) * (size_t)p->P * n;
+    if (cudaMalloc(&p->hs, tab) != cudaSuccess || cudaMalloc(&p->perm, tab) != cudaSuccess ||
+        cudaMalloc(&p->offs, sizeof(uint32_t) * (size_t)p->P * (b + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return OS_ERR_OOM;
+    }
+    *out = p;
+    return OS_OK;
+}
+
+}  // namespace
+
+}  // namespace osk
+
+using namespace osk;
+
+extern "C" os_status oversketch_plan(int64_t n, int32_t b, int32_t N, int32_t e, uint64_t seed,
+                                     void *stream, oversketch_plan_t *out) {
+    OSK_TRY(check_params(n, b, N, e, out));
+    Plan *p = nullptr;
+    OSK_TRY(alloc_plan(n, b, N, e, seed, &p));
+    cudaStream_t st = as_stream(stream);
+    const int64_t blocks_x = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    plan_hash_kernel<<<dim3((unsigned)blocks_x, (unsigned)p->P), 256, 0, st>>>(n, b, seed, p->hs);
+    os_status s = check_launch();
+    if (s == OS_OK) s = build_csr(p, st);
+    if (s != OS_OK) {
+        free_plan(p);
+        return s;
+    }
+    *out = reinterpret_cast<oversketch_plan_t>(p);
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_plan_from_tables(int64_t n, int32_t b, int32_t N, int32_t e,
+                                                 const uint32_t *h_host, const int8_t *sigma_host,
+                                                 void *stream, oversketch_plan_t *out) {
+    OSK_TRY(check_params(n, b, N, e, out));
+    if (!h_host || !sigma_host) return OS_ERR_INVALID_ARG;
+    const int P = N + e;
+    std::vector<uint32_t> packed((size_t)P * n);
+    for (size_t t = 0; t < packed.size(); ++t) {
+        if ((int64_t)h_host[t] >= b || (sigma_host[t] != 1 && sigma_host[t] != -1))
+            return OS_ERR_INVALID_ARG;
+        packed[t] = h_host[t] | (sigma_host[t] < 0 ? kSignBit : 0u);
+    }
+    Plan *p = nullptr;
+    OSK_TRY(alloc_plan(n, b, N, e, 0, &p));
+    cudaStream_t st = as_stream(stream);
+    os_status s = OS_OK;
+    if (cudaMemcpyAsync(p->hs, packed.data(), packed.size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        s = set_cuda_error(cudaGetLastError());
+    if (s == OS_OK) s = build_csr(p, st);
+    if (s != OS_OK) {
+        free_plan(p);
+        return s;
+    }
+    *out = reinterpret_cast<oversketch_plan_t>(p);
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_plan_get_tables(oversketch_plan_t plan, uint32_t *h_host,
+                                                int8_t *sigma_host, uint32_t *perm_host,
+                                                uint32_t *offs_host) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !h_host || !sigma_host) return OS_ERR_INVALID_ARG;
+    const size_t cnt = (size_t)p->P * p->n;
+    std::vector<uint32_t> packed(cnt);
+    OSK_CUDA_TRY(cudaMemcpy(packed.data(), p->hs, cnt * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    for (size_t t = 0; t < cnt; ++t) {
+        h_host[t] = packed[t] & kIndexMask;
+        sigma_host[t] = (packed[t] & kSignBit) ? (int8_t)-1 : (int8_t)1;
+    }
+    if (perm_host)
+        OSK_CUDA_TRY(cudaMemcpy(perm_host, p->perm, cnt * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (offs_host)
+        OSK_CUDA_TRY(cudaMemcpy(offs_host, p->offs, sizeof(uint32_t) * (size_t)p->P * (p->b + 1),
+                                cudaMemcpyDeviceToHost));
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_plan_info(oversketch_plan_t plan, int64_t *n, int32_t *b,
+                                          int32_t *N, int32_t *e) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p) return OS_ERR_INVALID_ARG;
+    if (n) *n = p->n;
+    if (b) *b = p->b;
+    if (N) *N = p->N;
+    if (e) *e = p->e;
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_plan_destroy(oversketch_plan_t plan) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p) return OS_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return OS_OK;
+}

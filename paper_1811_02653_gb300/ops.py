@@ -1,0 +1,341 @@
+"""Thin Python binding of liboversketch.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (without the
+``oversketch_`` prefix), passes device pointers of torch tensors and the
+current torch CUDA stream, and raises ``OverSketchError`` on a non-OK status.
+Tensors are allocated with torch (device memory is plumbing); every step of
+the computation runs in the library's kernels.  There is no fallback: if the
+library is missing or fails to load, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liboversketch.so")
+
+F32, BF16, FP8 = 0, 1, 2
+_DT = {torch.float32: F32, torch.bfloat16: BF16}
+if hasattr(torch, "float8_e4m3fn"):
+    _DT[torch.float8_e4m3fn] = FP8
+_TORCH_DT = {F32: torch.float32, BF16: torch.bfloat16, FP8: getattr(torch, "float8_e4m3fn", None)}
+DTYPE_NAMES = {"f32": F32, "fp32": F32, "bf16": BF16, "fp8": FP8, "fp8e4m3": FP8}
+FROB_WORKSPACE_BYTES = 12288
+
+_lib = None
+_lock = threading.Lock()
+
+
+class OverSketchError(RuntimeError):
+    pass
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("gemm_dtype", ctypes.c_int), ("col_scale", ctypes.c_void_p),
+                ("symmetric", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def load_library(path: str | None = None):
+    """Load liboversketch.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise OverSketchError(f"{p} is missing; build it with paper_1811_02653_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32, u64, f32, sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_float, ctypes.c_size_t)
+        st, pp = ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)
+        sigs = {
+            "oversketch_status_string": (ctypes.c_char_p, [st]),
+            "oversketch_last_cuda_error": (ctypes.c_char_p, []),
+            "oversketch_plan": (st, [i64, i32, i32, i32, u64, vp, pp]),
+            "oversketch_plan_from_tables": (st, [i64, i32, i32, i32, vp, vp, vp, pp]),
+            "oversketch_plan_get_tables": (st, [vp, vp, vp, vp, vp]),
+            "oversketch_plan_info": (st, [vp, vp, vp, vp, vp]),
+            "oversketch_plan_destroy": (st, [vp]),
+            "oversketch_sketch_left_workspace": (st, [vp, i64, st, ctypes.POINTER(sz)]),
+            "oversketch_sketch_left": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, vp, sz, vp]),
+            "oversketch_sketch_right": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp]),
+            "oversketch_gemm_masked": (st, [vp, vp, i64, vp, vp, i64, vp, st, i64, i64, u64, f32, f32,
+                                            vp, i64, vp]),
+            "oversketch_workspace_size": (st, [vp, i64, i64, st, ctypes.POINTER(_Opts), ctypes.POINTER(sz)]),
+            "oversketch_matmul": (st, [vp, vp, st, i64, vp, st, i64, vp, i64, i64, i64, i64, u64,
+                                       ctypes.POINTER(_Opts), vp, sz, vp]),
+            "oversketch_unsketch_cols": (st, [vp, vp, i64, i64, u64, f32, vp, st, i64, vp]),
+            "oversketch_unsketch_rows": (st, [vp, vp, i64, i64, u64, f32, vp, st, i64, vp]),
+            "oversketch_frob": (st, [vp, i64, vp, i64, i64, i64, vp, vp, sz, vp]),
+            "oversketch_device_status": (st, [vp, ctypes.POINTER(i32), i32]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols() -> list[str]:
+    return sorted(n for n in _sigs_names())
+
+
+def _sigs_names():
+    return ["oversketch_status_string", "oversketch_last_cuda_error", "oversketch_plan",
+            "oversketch_plan_from_tables", "oversketch_plan_get_tables", "oversketch_plan_info",
+            "oversketch_plan_destroy", "oversketch_sketch_left_workspace", "oversketch_sketch_left",
+            "oversketch_sketch_right", "oversketch_gemm_masked", "oversketch_workspace_size",
+            "oversketch_matmul", "oversketch_unsketch_cols", "oversketch_unsketch_rows",
+            "oversketch_frob", "oversketch_device_status"]
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        lib = load_library()
+        msg = lib.oversketch_status_string(status).decode()
+        if status == 5:
+            msg += " (" + lib.oversketch_last_cuda_error().decode() + ")"
+        raise OverSketchError(f"{what}: {msg}")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype not in _DT:
+        raise OverSketchError(f"unsupported dtype {t.dtype}")
+    return _DT[t.dtype]
+
+
+def _dtype_code(d) -> int:
+    if isinstance(d, str):
+        return DTYPE_NAMES[d.lower()]
+    if isinstance(d, torch.dtype):
+        return _DT[d]
+    return int(d)
+
+
+def _rowmajor(t: torch.Tensor, name: str):
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise OverSketchError(f"{name} must be a row-major 2-D tensor")
+    if not t.is_cuda:
+        raise OverSketchError(f"{name} must live on a CUDA device")
+    return t.stride(0)
+
+
+def _pad_ld(cols: int, dtype_code: int) -> int:
+    el = 16 // (4 if dtype_code == F32 else (2 if dtype_code == BF16 else 1))
+    return (cols + el - 1) // el * el
+
+
+class Plan:
+    """The sketch S of Eq. 3 on the device (oversketch_plan)."""
+
+    def __init__(self, n: int, b: int, N: int, e: int, seed: int = 0, stream=None,
+                 tables=None):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        if tables is None:
+            _check(lib.oversketch_plan(n, b, N, e, seed & (2 ** 64 - 1), _stream(stream),
+                                       ctypes.byref(h)), "oversketch_plan")
+        else:
+            hh, ss = tables
+            hh = np.ascontiguousarray(hh, dtype=np.uint32)
+            ss = np.ascontiguousarray(ss, dtype=np.int8)
+            assert hh.shape == (N + e, n) and ss.shape == (N + e, n)
+            _check(lib.oversketch_plan_from_tables(n, b, N, e, hh.ctypes.data_as(ctypes.c_void_p),
+                                                   ss.ctypes.data_as(ctypes.c_void_p),
+                                                   _stream(stream), ctypes.byref(h)),
+                   "oversketch_plan_from_tables")
+        self._h = h
+        self.n, self.b, self.N, self.e, self.seed = n, b, N, e, seed
+        self.P = N + e
+        self.z = self.P * b
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tables(self):
+        """(h, sigma, perm, offs) copied to host numpy arrays."""
+        lib = load_library()
+        h = np.empty((self.P, self.n), np.uint32)
+        s = np.empty((self.P, self.n), np.int8)
+        perm = np.empty((self.P, self.n), np.uint32)
+        offs = np.empty((self.P, self.b + 1), np.uint32)
+        _check(lib.oversketch_plan_get_tables(self._h, h.ctypes.data_as(ctypes.c_void_p),
+                                              s.ctypes.data_as(ctypes.c_void_p),
+                                              perm.ctypes.data_as(ctypes.c_void_p),
+                                              offs.ctypes.data_as(ctypes.c_void_p)),
+               "oversketch_plan_get_tables")
+        return h, s, perm, offs
+
+    def destroy(self):
+        if self._h:
+            load_library().oversketch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def plan(n, b, N, e, seed=0, stream=None) -> Plan:
+    return Plan(n, b, N, e, seed, stream)
+
+
+def plan_from_tables(h, sigma, b, N, e, stream=None) -> Plan:
+    P, n = np.asarray(h).shape
+    return Plan(n, b, N, e, 0, stream, tables=(h, sigma))
+
+
+def _fp8_scales_shape(rows, z):
+    return (rows, (z + 127) // 128)
+
+
+def sketch_left_workspace(p: Plan, m: int, a_dtype=torch.float32) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().oversketch_sketch_left_workspace(p.handle, m, _dtype_code(a_dtype),
+                                                           ctypes.byref(out)),
+           "oversketch_sketch_left_workspace")
+    return out.value
+
+
+def sketch_left(p: Plan, A: torch.Tensor, out_dtype="f32", col_scale=None, out=None,
+                scales=None, workspace=None, stream=None):
+    """A~ = A diag(col_scale) S (m x z, K-major); returns (At, scales or None)."""
+    lda = _rowmajor(A, "A")
+    m = A.shape[0]
+    od = _dtype_code(out_dtype)
+    ld = _pad_ld(p.z, od)
+    if out is None:
+        out = torch.empty((m, ld), dtype=_TORCH_DT[od], device=A.device)[:, :p.z]
+    if od == FP8 and scales is None:
+        scales = torch.empty(_fp8_scales_shape(m, p.z), dtype=torch.float32, device=A.device)
+    if workspace is None:
+        workspace = torch.empty(sketch_left_workspace(p, m, A.dtype), dtype=torch.uint8, device=A.device)
+    _check(load_library().oversketch_sketch_left(
+        p.handle, _ptr(A), _dt(A), m, lda, _ptr(out), od, out.stride(0), _ptr(scales),
+        _ptr(col_scale), _ptr(workspace), workspace.numel(), _stream(stream)), "oversketch_sketch_left")
+    return out, scales
+
+
+def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=None, stream=None):
+    """B~^T = (S^T B)^T (l x z, K-major); returns (BtT, scales or None)."""
+    ldb = _rowmajor(B, "B")
+    l = B.shape[1]
+    od = _dtype_code(out_dtype)
+    ld = _pad_ld(p.z, od)
+    if out is None:
+        out = torch.empty((l, ld), dtype=_TORCH_DT[od], device=B.device)[:, :p.z]
+    if od == FP8 and scales is None:
+        scales = torch.empty(_fp8_scales_shape(l, p.z), dtype=torch.float32, device=B.device)
+    _check(load_library().oversketch_sketch_right(
+        p.handle, _ptr(B), _dt(B), l, ldb, _ptr(out), od, out.stride(0), _ptr(scales), _stream(stream)),
+        "oversketch_sketch_right")
+    return out, scales
+
+
+def gemm_masked(p: Plan, At, BtT, mask: int, alpha=None, beta=0.0, C=None, a_scales=None,
+                b_scales=None, stream=None):
+    """C = alpha * sum_{j in mask} At_j BtT_j^T (+ beta C); alpha defaults to 1/k."""
+    m, l = At.shape[0], BtT.shape[0]
+    if alpha is None:
+        alpha = 1.0 / bin(mask).count("1")
+    if C is None:
+        C = torch.empty((m, l), dtype=torch.float32, device=At.device)
+    _check(load_library().oversketch_gemm_masked(
+        p.handle, _ptr(At), At.stride(0), _ptr(a_scales), _ptr(BtT), BtT.stride(0), _ptr(b_scales),
+        _dt(At), m, l, mask, alpha, beta, _ptr(C), C.stride(0), _stream(stream)), "oversketch_gemm_masked")
+    return C
+
+
+def _opts(gemm_dtype, col_scale=None, symmetric=False):
+    return _Opts(_dtype_code(gemm_dtype), col_scale.data_ptr() if col_scale is not None else None,
+                 1 if symmetric else 0, 0)
+
+
+def workspace_size(p: Plan, m: int, l: int, a_dtype=torch.float32, gemm_dtype="f32",
+                   symmetric=False) -> int:
+    out = ctypes.c_size_t()
+    o = _opts(gemm_dtype, None, symmetric)
+    _check(load_library().oversketch_workspace_size(p.handle, m, l, _dtype_code(a_dtype),
+                                                    ctypes.byref(o), ctypes.byref(out)),
+           "oversketch_workspace_size")
+    return out.value
+
+
+def matmul(p: Plan, A, B, mask: int, gemm_dtype="f32", col_scale=None, symmetric=False, C=None,
+           workspace=None, stream=None):
+    """The whole OverSketch product (A S)(S^T B)/k over the kept blocks."""
+    lda = _rowmajor(A, "A")
+    m, n = A.shape
+    if symmetric:
+        l, ldb, bt, bp = m, 0, F32, None
+    else:
+        ldb = _rowmajor(B, "B")
+        l, bt, bp = B.shape[1], _dt(B), _ptr(B)
+    if C is None:
+        C = torch.empty((m, l), dtype=torch.float32, device=A.device)
+    o = _opts(gemm_dtype, col_scale, symmetric)
+    if workspace is None:
+        workspace = torch.empty(workspace_size(p, m, l, A.dtype, gemm_dtype, symmetric),
+                                dtype=torch.uint8, device=A.device)
+    _check(load_library().oversketch_matmul(
+        p.handle, _ptr(A), _dt(A), lda, bp, bt, ldb, _ptr(C), C.stride(0), m, n, l, mask,
+        ctypes.byref(o), _ptr(workspace), workspace.numel(), _stream(stream)), "oversketch_matmul")
+    return C
+
+
+def unsketch_cols(p: Plan, T, mask: int, scale: float, out_dtype="f32", out=None, stream=None):
+    m = T.shape[0]
+    od = _dtype_code(out_dtype)
+    if out is None:
+        out = torch.empty((m, p.n), dtype=_TORCH_DT[od], device=T.device)
+    _check(load_library().oversketch_unsketch_cols(
+        p.handle, _ptr(T), m, T.stride(0), mask, scale, _ptr(out), od, out.stride(0), _stream(stream)),
+        "oversketch_unsketch_cols")
+    return out
+
+
+def unsketch_rows(p: Plan, U, mask: int, scale: float, out_dtype="f32", out=None, stream=None):
+    l = U.shape[1]
+    od = _dtype_code(out_dtype)
+    if out is None:
+        out = torch.empty((p.n, l), dtype=_TORCH_DT[od], device=U.device)
+    _check(load_library().oversketch_unsketch_rows(
+        p.handle, _ptr(U), l, U.stride(0), mask, scale, _ptr(out), od, out.stride(0), _stream(stream)),
+        "oversketch_unsketch_rows")
+    return out
+
+
+def frob(X, Y=None, stream=None):
+    """(sum (X-Y)^2, sum Y^2, sum X*Y) in FP64 on the device (Def. 4.1's norms)."""
+    out = torch.empty(3, dtype=torch.float64, device=X.device)
+    ws = torch.empty(FROB_WORKSPACE_BYTES, dtype=torch.uint8, device=X.device)
+    _check(load_library().oversketch_frob(
+        _ptr(X), X.stride(0), _ptr(Y), Y.stride(0) if Y is not None else 0, X.shape[0], X.shape[1],
+        _ptr(out), _ptr(ws), ws.numel(), _stream(stream)), "oversketch_frob")
+    return out
+
+
+def device_status(reset=True, stream=None) -> int:
+    """0 (OS_OK) or 6 (OS_ERR_TIMEOUT) from the tensor-core kernels' status word."""
+    out = ctypes.c_int32()
+    _check(load_library().oversketch_device_status(_stream(stream), ctypes.byref(out), 1 if reset else 0),
+           "oversketch_device_status")
+    return out.value

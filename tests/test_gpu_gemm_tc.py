@@ -1,0 +1,123 @@
+"""GPU parity of the tensor-core (tcgen05) masked GEMM and of the BF16
+OverSketch path, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import gpu_lib
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_1811_02653_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ops():
+    return gpu_lib()
+
+
+def _bf16(x):
+    """Host FP32 -> device BF16 and the exact FP64 values of those BF16 numbers."""
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16).cuda()
+    return t, t.float().cpu().numpy().astype(np.float64)
+
+
+GEMM_CASES = [
+    # m, l, b, N, e, mask
+    (128, 256, 64, 2, 1, 0b011),           # one tile, one K block per sketch block
+    (256, 512, 256, 4, 1, 0b11011),        # small workload's block shape
+    (300, 700, 128, 3, 2, 0b10101),        # ragged m and l, non-contiguous kept blocks
+    (1, 1, 64, 1, 0, 0b1),                 # single element
+    (1000, 130, 1024, 2, 1, 0b110),        # K = 2048, l < tile width
+    (640, 1536, 512, 8, 2, 0b1110111101),  # many tiles (persistent loop, both TMEM buffers)
+]
+
+
+@pytest.mark.parametrize("m,l,b,N,e,mask", GEMM_CASES)
+def test_gemm_bf16_parity(ops, m, l, b, N, e, mask):
+    rng = np.random.default_rng(m * 31 + l)
+    z = (N + e) * b
+    At, At64 = _bf16(rng.standard_normal((m, z)))
+    Bt, Bt64 = _bf16(rng.standard_normal((l, z)))
+    p = ops.plan(max(z, 64), b, N, e, 0)
+    C = ops.gemm_masked(p, At, Bt, mask).cpu().numpy()
+    ref = oracle.masked_product(At64, Bt64.T, b, mask)
+    k = bin(mask).count("1")
+    K = k * b
+    absref = oracle.masked_product(np.abs(At64), np.abs(Bt64).T, b, mask)
+    bound = 2 * K * 2.0 ** -24 * absref + 1e-30
+    assert (np.abs(C - ref) <= bound).all()
+    assert oracle.rel_frob(C, ref) <= 1e-5
+
+
+def test_gemm_bf16_alpha_beta(ops):
+    rng = np.random.default_rng(7)
+    b, N, e = 128, 3, 1
+    z = (N + e) * b
+    At, At64 = _bf16(rng.standard_normal((200, z)))
+    Bt, Bt64 = _bf16(rng.standard_normal((300, z)))
+    C0 = rng.standard_normal((200, 300)).astype(np.float32)
+    C = torch.from_numpy(C0.copy()).cuda()
+    p = ops.plan(1024, b, N, e, 0)
+    ops.gemm_masked(p, At, Bt, 0b1011, alpha=0.25, beta=-1.5, C=C)
+    ref = 0.25 * 3 * oracle.masked_product(At64, Bt64.T, b, 0b1011) - 1.5 * C0
+    assert oracle.rel_frob(C.cpu().numpy(), ref) <= 1e-5
+
+
+def test_gemm_bf16_reproducible(ops):
+    rng = np.random.default_rng(8)
+    b, N, e = 256, 4, 1
+    z = (N + e) * b
+    At, _ = _bf16(rng.standard_normal((512, z)))
+    Bt, _ = _bf16(rng.standard_normal((768, z)))
+    p = ops.plan(4096, b, N, e, 0)
+    C1 = ops.gemm_masked(p, At, Bt, 0b10111)
+    C2 = ops.gemm_masked(p, At, Bt, 0b10111)
+    assert torch.equal(C1, C2)
+    assert ops.device_status() == 0
+
+
+def _bf16_oracle(A, B, w, h, s):
+    At_q = oracle.round_bf16(oracle.sketch_left(A, h, s, w.b))
+    Bt_q = oracle.round_bf16(oracle.sketch_right(B, h, s, w.b))
+    return oracle.masked_product(At_q, Bt_q, w.b, w.mask)
+
+
+def test_small_workload_bf16(ops):
+    w = W.SMALL
+    A, B = w.left(), w.right()
+    p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
+    C = ops.matmul(p, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), w.mask, "bf16")
+    h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+    assert oracle.rel_frob(C.cpu().numpy(), _bf16_oracle(A, B, w, h, s)) <= 1e-4
+
+
+@pytest.mark.parametrize("m,n,l,b,N,e,mask", [(300, 5000, 200, 128, 3, 1, 0b1101),
+                                              (130, 4096, 1000, 1024, 2, 1, 0b011)])
+def test_matmul_bf16_parity(ops, m, n, l, b, N, e, mask):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    B = rng.standard_normal((n, l)).astype(np.float32)
+    w = W.Workload("t", m, n, l, b, N, e, mask)
+    p = ops.plan(n, b, N, e, 3)
+    C = ops.matmul(p, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), mask, "bf16")
+    h, s = oracle.hash_tables(n, b, N, e, 3)
+    assert oracle.rel_frob(C.cpu().numpy(), _bf16_oracle(A, B, w, h, s)) <= 1e-4
+
+
+def test_symmetric_product(ops):
+    # H = (1/k) A~_sel A~_sel^T with the column scale sqrt(D) (Sec. 5.2's Hessian form)
+    m, n, b, N, e, mask = 256, 8192, 256, 6, 1, 0b1110111
+    rng = np.random.default_rng(9)
+    A = (rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.05)).astype(np.float32)
+    cs = np.sqrt(10.0 ** rng.uniform(-6, 6, n)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 0)
+    H = ops.matmul(p, torch.from_numpy(A).cuda(), None, mask, "bf16",
+                   col_scale=torch.from_numpy(cs).cuda(), symmetric=True).cpu().numpy()
+    h, s = oracle.hash_tables(n, b, N, e, 0)
+    At_q = oracle.round_bf16(oracle.sketch_left(A, h, s, b, cs))
+    ref = oracle.masked_product(At_q, At_q.T, b, mask)
+    assert oracle.rel_frob(H, ref) <= 1e-4
+    assert oracle.rel_frob(H, H.T) <= 1e-6

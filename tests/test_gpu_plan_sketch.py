@@ -1,0 +1,209 @@
+"""GPU parity of the plan (bit-exact) and of the sketch kernels (within the
+FP32 rounding bound of each output), through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import (assert_bf16_within, assert_fp32_within, assert_fp8_within, gpu_lib,
+                     sketch_bounds_left, sketch_bounds_right)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ops():
+    return gpu_lib()
+
+
+def _dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+PLAN_CASES = [
+    (4096, 256, 4, 1, 0),          # small workload plan
+    (65536, 1024, 8, 2, 0),        # square workload plan
+    (5000, 1, 3, 1, 7),            # b = 1: every index in one bucket
+    (37, 64, 2, 1, 3),             # b >= n
+    (9999, 128, 60, 4, 11),        # N + e = 64, n not a multiple of the chunk
+    (1, 16, 1, 0, 5),              # n = 1, e = 0
+    (300_000, 4096, 6, 1, 0),      # wide buckets, many chunks
+]
+
+
+@pytest.mark.parametrize("n,b,N,e,seed", PLAN_CASES)
+def test_plan_tables_bit_exact(ops, n, b, N, e, seed):
+    p = ops.plan(n, b, N, e, seed)
+    h, s, perm, offs = p.tables()
+    h_ref, s_ref = oracle.hash_tables(n, b, N, e, seed)
+    assert np.array_equal(h, h_ref)
+    assert np.array_equal(s, s_ref)
+    # bucket-CSR: stable counting sort of every block by bucket
+    for j in range(N + e):
+        order = np.argsort(h_ref[j], kind="stable")
+        exp_perm = order.astype(np.uint32) | np.where(s_ref[j][order] < 0, np.uint32(1 << 31), np.uint32(0))
+        assert np.array_equal(perm[j], exp_perm)
+        cnt = np.bincount(h_ref[j].astype(np.int64), minlength=b)
+        assert np.array_equal(offs[j], np.concatenate([[0], np.cumsum(cnt)]).astype(np.uint32))
+    p.destroy()
+
+
+def test_plan_from_tables_eq2(ops):
+    ScT = np.array([[0, 0, 0, 1, -1, 0, -1, 0, 0], [1, -1, 0, 0, 0, 1, 0, 0, 0],
+                    [0, 0, 1, 0, 0, 0, 0, -1, -1]], dtype=np.float64)
+    h, s = oracle.tables_from_sketch_matrix(ScT.T)
+    p = ops.plan_from_tables(h, s, 3, 1, 0)
+    hh, ss, _, _ = p.tables()
+    assert np.array_equal(hh, h) and np.array_equal(ss, s)
+    A = np.random.default_rng(0).standard_normal((5, 9)).astype(np.float32)
+    At, _ = ops.sketch_left(p, _dev(A), "f32")
+    ref, bound = sketch_bounds_left(A, h, s, 3)
+    assert_fp32_within(At.cpu().numpy(), ref, bound)
+    # identity in: S_c out (exact)
+    I = np.eye(9, dtype=np.float32)
+    At, _ = ops.sketch_left(p, _dev(I), "f32")
+    assert np.array_equal(At.cpu().numpy().astype(np.float64), ScT.T)
+
+
+def test_plan_rejects_bad_tables(ops):
+    with pytest.raises(ops.OverSketchError):
+        ops.plan_from_tables(np.array([[5, 0]], np.uint32), np.array([[1, 1]], np.int8), 3, 1, 0)
+    with pytest.raises(ops.OverSketchError):
+        ops.plan(10, 4, 64, 1)
+
+
+SKETCH_CASES = [
+    # m, n, l, b, N, e
+    (512, 4096, 512, 256, 4, 1),       # small workload
+    (300, 2000, 130, 128, 3, 2),       # ragged tiles, free dims not multiples of 128
+    (7, 513, 5, 32, 2, 1),             # tiny, odd sizes
+    (129, 4096, 257, 1024, 2, 1),      # one bucket per CTA tile row
+]
+
+
+@pytest.mark.parametrize("m,n,l,b,N,e", SKETCH_CASES)
+def test_sketch_fp32_parity(ops, m, n, l, b, N, e):
+    rng = np.random.default_rng(m * 7 + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    B = rng.standard_normal((n, l)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 0)
+    h, s = oracle.hash_tables(n, b, N, e, 0)
+    At, _ = ops.sketch_left(p, _dev(A), "f32")
+    BtT, _ = ops.sketch_right(p, _dev(B), "f32")
+    ref_l, bd_l = sketch_bounds_left(A, h, s, b)
+    ref_r, bd_r = sketch_bounds_right(B, h, s, b)
+    assert_fp32_within(At.cpu().numpy(), ref_l, bd_l)
+    assert_fp32_within(BtT.cpu().numpy(), ref_r.T, bd_r.T)
+    # bitwise reproducible (fixed order, no atomics)
+    At2, _ = ops.sketch_left(p, _dev(A), "f32")
+    assert torch.equal(At, At2)
+
+
+def test_sketch_col_scale(ops):
+    m, n, b, N, e = 64, 3000, 256, 3, 1
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    cs = np.sqrt(10.0 ** rng.uniform(-6, 6, n)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 1)
+    h, s = oracle.hash_tables(n, b, N, e, 1)
+    At, _ = ops.sketch_left(p, _dev(A), "f32", col_scale=_dev(cs))
+    ref, bd = sketch_bounds_left(A, h, s, b, cs)
+    assert_fp32_within(At.cpu().numpy(), ref, bd)
+
+
+@pytest.mark.parametrize("m,n,l,b,N,e", [(512, 4096, 512, 256, 4, 1), (200, 3000, 70, 128, 2, 1)])
+def test_sketch_bf16_parity(ops, m, n, l, b, N, e):
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    B = rng.standard_normal((n, l)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 0)
+    h, s = oracle.hash_tables(n, b, N, e, 0)
+    At, _ = ops.sketch_left(p, _dev(A), "bf16")
+    BtT, _ = ops.sketch_right(p, _dev(B), "bf16")
+    ref_l, bd_l = sketch_bounds_left(A, h, s, b)
+    ref_r, bd_r = sketch_bounds_right(B, h, s, b)
+    assert_bf16_within(At.float().cpu().numpy(), ref_l, bd_l)
+    assert_bf16_within(BtT.float().cpu().numpy(), ref_r.T, bd_r.T)
+
+
+def test_sketch_bf16_input(ops):
+    # BF16 operands (the autograd workload's dtype) are read exactly
+    m, n, l, b = 96, 4096, 80, 256
+    rng = np.random.default_rng(12)
+    A = (rng.standard_normal((m, n)) * 0.02).astype(np.float32)
+    B = (rng.standard_normal((n, l)) * 0.02).astype(np.float32)
+    Ab, Bb = _dev(A, torch.bfloat16), _dev(B, torch.bfloat16)
+    A64 = Ab.float().cpu().numpy()
+    B64 = Bb.float().cpu().numpy()
+    p = ops.plan(n, b, 4, 1, 0)
+    h, s = oracle.hash_tables(n, b, 4, 1, 0)
+    At, _ = ops.sketch_left(p, Ab, "f32")
+    BtT, _ = ops.sketch_right(p, Bb, "f32")
+    ref_l, bd_l = sketch_bounds_left(A64, h, s, b)
+    ref_r, bd_r = sketch_bounds_right(B64, h, s, b)
+    assert_fp32_within(At.cpu().numpy(), ref_l, bd_l)
+    assert_fp32_within(BtT.cpu().numpy(), ref_r.T, bd_r.T)
+
+
+@pytest.mark.parametrize("m,n,l,b,N,e", [(256, 4096, 384, 256, 4, 1), (100, 5000, 33, 128, 3, 1)])
+def test_sketch_fp8_parity(ops, m, n, l, b, N, e):
+    rng = np.random.default_rng(13)
+    A = (rng.standard_normal((m, n)) * np.exp(rng.standard_normal((m, 1)) * 3)).astype(np.float32)
+    B = rng.standard_normal((n, l)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 0)
+    h, s = oracle.hash_tables(n, b, N, e, 0)
+    At, sa = ops.sketch_left(p, _dev(A), "fp8")
+    BtT, sb = ops.sketch_right(p, _dev(B), "fp8")
+    ref_l, bd_l = sketch_bounds_left(A, h, s, b)
+    ref_r, bd_r = sketch_bounds_right(B, h, s, b)
+    assert_fp8_within(At.float().cpu().numpy(), sa.cpu().numpy(), ref_l, bd_l)
+    assert_fp8_within(BtT.float().cpu().numpy(), sb.cpu().numpy(), ref_r.T, bd_r.T)
+
+
+def test_sketch_argument_errors(ops):
+    p = ops.plan(1000, 100, 2, 1, 0)          # b = 100: FP8 needs b % 128 == 0
+    A = torch.zeros((4, 1000), device="cuda")
+    with pytest.raises(ops.OverSketchError):
+        ops.sketch_left(p, A, "fp8")
+    with pytest.raises(ops.OverSketchError):
+        ops.sketch_left(p, torch.zeros((4, 999), device="cuda"), "f32")   # lda < n
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ops.OverSketchError):
+        ops.sketch_left(p, A, "f32", workspace=ws)                         # workspace too small
+
+
+def test_unsketch_parity(ops):
+    m, n, l, b, N, e = 64, 3000, 96, 128, 4, 1
+    mask = 0b10111
+    rng = np.random.default_rng(14)
+    z = (N + e) * b
+    T = rng.standard_normal((m, z)).astype(np.float32)
+    U = rng.standard_normal((z, l)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 2)
+    h, s = oracle.hash_tables(n, b, N, e, 2)
+    dX = ops.unsketch_cols(p, _dev(T), mask, 0.25).cpu().numpy()
+    dG = ops.unsketch_rows(p, _dev(U), mask, 0.25).cpu().numpy()
+    ref_x = oracle.unsketch_cols(T, h, s, b, mask, 0.25)
+    ref_g = oracle.unsketch_rows(U, h, s, b, mask, 0.25)
+    # 4 kept terms: FP32 bound with 5 roundings (4 adds + the scale)
+    bx = 5 * 2.0 ** -24 * oracle.unsketch_cols(np.abs(T), h, np.ones_like(s), b, mask, 0.25) + 1e-30
+    bg = 5 * 2.0 ** -24 * oracle.unsketch_rows(np.abs(U), h, np.ones_like(s), b, mask, 0.25) + 1e-30
+    assert_fp32_within(dX, ref_x, bx)
+    assert_fp32_within(dG, ref_g, bg)
+
+
+def test_frob_fp64(ops):
+    rng = np.random.default_rng(15)
+    X = rng.standard_normal((300, 500)).astype(np.float32)
+    Y = rng.standard_normal((300, 500)).astype(np.float32)
+    out = ops.frob(_dev(X), _dev(Y)).cpu().numpy()
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    ref = [((X64 - Y64) ** 2).sum(), (Y64 ** 2).sum(), (X64 * Y64).sum()]
+    assert np.allclose(out, ref, rtol=1e-12, atol=0)
+    out1 = ops.frob(_dev(X)).cpu().numpy()
+    assert np.isclose(out1[0], (X64 ** 2).sum(), rtol=1e-12)
+    assert np.array_equal(out, ops.frob(_dev(X), _dev(Y)).cpu().numpy())
