@@ -227,12 +227,15 @@ def run_ours(args):
     At, a_sc = ops.sketch_left(p, A, gd)
     BtT, b_sc = ops.sketch_right(p, B, gd)
     C = torch.empty((w.m, w.l), dtype=torch.float32, device=dev)
-    ws_left = torch.empty(ops.sketch_left_workspace(p, w.m), dtype=torch.uint8, device=dev)
+    # one packed-strip workspace, reused by the left and then the right sketch (as oversketch_matmul does)
+    ws_pack = torch.empty(max(ops.sketch_workspace(p, w.m), ops.sketch_workspace(p, w.l)),
+                          dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    # the same three calls oversketch_matmul makes: only kept blocks are sketched
     def step():
-        ops.sketch_left(p, A, gd, out=At, scales=a_sc, workspace=ws_left)
-        ops.sketch_right(p, B, gd, out=BtT, scales=b_sc)
+        ops.sketch_left(p, A, gd, out=At, scales=a_sc, workspace=ws_pack, block_mask=w.mask)
+        ops.sketch_right(p, B, gd, out=BtT, scales=b_sc, block_mask=w.mask, workspace=ws_pack)
         ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc)
 
     for _ in range(args.warmup):
@@ -254,9 +257,9 @@ def run_ours(args):
     for s in range(args.steps):
         e = ev[s]
         e[0].record(stream)
-        ops.sketch_left(p, A, gd, out=At, scales=a_sc, workspace=ws_left)
+        ops.sketch_left(p, A, gd, out=At, scales=a_sc, workspace=ws_pack, block_mask=w.mask)
         e[1].record(stream)
-        ops.sketch_right(p, B, gd, out=BtT, scales=b_sc)
+        ops.sketch_right(p, B, gd, out=BtT, scales=b_sc, block_mask=w.mask, workspace=ws_pack)
         e[2].record(stream)
         ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc)
         e[3].record(stream)
@@ -303,9 +306,10 @@ def run_ours(args):
     # ---- dominant kernel and its roofline ----
     es = {"bf16": 2, "f32": 4, "fp8": 1}[gd]
     n_kept = w.k
-    right_bytes = w.n * w.l * 4 + w.l * z * es
+    right_bytes = w.n * w.l * 4 + w.l * n_kept * w.b * es
     gemm_flop = 2.0 * w.m * n_kept * w.b * w.l
-    phases = {"sketch_left (transpose + gather)": t_left, "sketch_right": t_right, "gemm_masked": t_gemm}
+    phases = {"sketch_left (pack + gather)": t_left, "sketch_right (pack + gather)": t_right,
+              "gemm_masked": t_gemm}
     if t_gemm >= t_right:
         dom = "gemm_masked_bf16_kernel" if gd == "bf16" else "gemm_masked_f32_kernel"
         if gd == "bf16":
@@ -362,7 +366,7 @@ def run_ours(args):
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * flop_eff / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 4 * args.steps, "clocks": clk, "error": err}
+            "gpu_launches": 5 * args.steps, "clocks": clk, "error": err}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -131,25 +131,31 @@ OS_API os_status oversketch_plan_destroy(oversketch_plan_t plan);
  *     of (sum / 2^e_rt).  NULL otherwise.  FP8 needs b % 128 == 0.
  *   Sums are accumulated in FP32 in ascending order of i inside a bucket;
  *   BF16 output is the round-to-nearest-even of that FP32 sum.
- *   workspace: device memory of at least oversketch_sketch_left_workspace()
- *   bytes (the kernel stages A^T there), 256-byte aligned.
+ *   block_mask: bit j set = compute the columns of block j; 0 = all blocks.
+ *     Columns of blocks not listed are left untouched (the paper's remark
+ *     that blocks missed while sketching become stragglers of the product).
+ *   workspace: device memory of at least oversketch_sketch_workspace(plan, m,
+ *     a_t) bytes; the operand is packed there strip-major (32 free indices
+ *     per strip, n rows each) before the bucket gather.
  * oversketch_sketch_right:
  *   BtT[c, j*b + q] = sum_{i : h_j(i) = q} sigma_j(i) * B[i, c]
- *   B: n x l (ldb >= l); BtT: l x z (ldbt >= z); scales l x (z/128) for FP8.
- *   No workspace needed.
+ *   B: n x l (ldb >= l); BtT: l x z (ldbt >= z); scales l x (z/128) for FP8;
+ *   block_mask as above; workspace of oversketch_sketch_workspace(plan, l, b_t)
+ *   bytes.
  * Errors: OS_ERR_INVALID_ARG (null pointers, ld too small, out pointers or
  *   ld not 16-byte aligned), OS_ERR_DTYPE, OS_ERR_UNSUPPORTED,
  *   OS_ERR_WORKSPACE, OS_ERR_CUDA (launch failure).
  */
-OS_API os_status oversketch_sketch_left_workspace(oversketch_plan_t plan, int64_t m, os_dtype a_t,
-                                           size_t *bytes);
+OS_API os_status oversketch_sketch_workspace(oversketch_plan_t plan, int64_t free_extent, os_dtype in_t,
+                                      size_t *bytes);
 OS_API os_status oversketch_sketch_left(oversketch_plan_t plan, const void *A, os_dtype a_t, int64_t m,
                                  int64_t lda, void *At, os_dtype out_t, int64_t ldat, float *scales,
-                                 const float *col_scale, void *workspace, size_t ws_bytes,
-                                 void *stream);
+                                 const float *col_scale, uint64_t block_mask, void *workspace,
+                                 size_t ws_bytes, void *stream);
 OS_API os_status oversketch_sketch_right(oversketch_plan_t plan, const void *B, os_dtype b_t, int64_t l,
                                   int64_t ldb, void *BtT, os_dtype out_t, int64_t ldbt,
-                                  float *scales, void *stream);
+                                  float *scales, uint64_t block_mask, void *workspace,
+                                  size_t ws_bytes, void *stream);
 
 /* -------------------------------------------------------------------------
  * Masked block-sum GEMM (Alg. 3 computation + termination + reduction; the
@@ -183,7 +189,7 @@ typedef struct {
 } os_opts;
 
 OS_API os_status oversketch_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
-                                    os_dtype a_t, const os_opts *opts, size_t *bytes);
+                                    os_dtype a_t, os_dtype b_t, const os_opts *opts, size_t *bytes);
 OS_API os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os_dtype a_t, int64_t lda,
                             const void *B, os_dtype b_t, int64_t ldb, float *C, int64_t ldc,
                             int64_t m, int64_t n, int64_t l, uint64_t mask, const os_opts *opts,

@@ -8,12 +8,14 @@
 namespace osk {
 
 // implemented in sketch.cu / gemm_simt.cu / gemm_tc.cu
-size_t left_workspace_bytes(const Plan *p, int64_t m, os_dtype a_t);
+size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t);
 os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
-                           const float *col_scale, void *ws, size_t ws_bytes, cudaStream_t st);
+                           const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
+                           cudaStream_t st);
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
-                            void *BtT, os_dtype out_t, int64_t ldbt, float *scales, cudaStream_t st);
+                            void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
+                            void *ws, size_t ws_bytes, cudaStream_t st);
 os_status gemm_masked_f32(const Plan *p, const float *At, int64_t ldat, const float *BtT,
                           int64_t ldbt, int64_t m, int64_t l, uint64_t mask, float alpha, float beta,
                           float *C, int64_t ldc, cudaStream_t st);
@@ -61,7 +63,7 @@ struct MatmulLayout {
     size_t at_bytes, bt_bytes, as_bytes, bs_bytes, left_ws;
 };
 
-MatmulLayout layout(const Plan *p, int64_t m, int64_t l, os_dtype a_t, const os_opts *o) {
+MatmulLayout layout(const Plan *p, int64_t m, int64_t l, os_dtype a_t, os_dtype b_t, const os_opts *o) {
     MatmulLayout L;
     const os_dtype g = o ? o->gemm_dtype : OS_F32;
     const size_t es = dtype_size(g);
@@ -75,7 +77,10 @@ MatmulLayout layout(const Plan *p, int64_t m, int64_t l, os_dtype a_t, const os_
     L.bt_bytes = sym ? 0 : align256((size_t)l * L.ldbt * es);
     L.as_bytes = g == OS_FP8E4M3 ? align256((size_t)m * L.nsl * 4) : 0;
     L.bs_bytes = (g == OS_FP8E4M3 && !sym) ? align256((size_t)l * L.nsl * 4) : 0;
-    L.left_ws = align256(left_workspace_bytes(p, m, a_t));
+    // the packed-strip buffer is reused by the left and then the right sketch
+    const size_t wl = sketch_workspace_bytes(p, m, a_t);
+    const size_t wr = sym ? 0 : sketch_workspace_bytes(p, l, b_t);
+    L.left_ws = align256(wl > wr ? wl : wr);
     return L;
 }
 
@@ -170,10 +175,11 @@ extern "C" os_status oversketch_gemm_masked(oversketch_plan_t plan, const void *
 }
 
 extern "C" os_status oversketch_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
-                                               os_dtype a_t, const os_opts *opts, size_t *bytes) {
+                                               os_dtype a_t, os_dtype b_t, const os_opts *opts,
+                                               size_t *bytes) {
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     if (!p || !bytes || m < 0 || l < 0) return OS_ERR_INVALID_ARG;
-    const MatmulLayout L = layout(p, m, l, a_t, opts);
+    const MatmulLayout L = layout(p, m, l, a_t, b_t, opts);
     *bytes = L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes + L.left_ws + 256;
     return OS_OK;
 }
@@ -192,7 +198,7 @@ extern "C" os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os
     OSK_TRY(check_mask(mask, p->P));
     const os_dtype g = opts ? opts->gemm_dtype : OS_F32;
     if (g != OS_F32 && g != OS_BF16 && g != OS_FP8E4M3) return OS_ERR_DTYPE;
-    const MatmulLayout L = layout(p, m, l, a_t, opts);
+    const MatmulLayout L = layout(p, m, l, a_t, b_t, opts);
     const size_t need = L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes + L.left_ws + 256;
     if (!workspace || ws_bytes < need) return OS_ERR_WORKSPACE;
     if (m == 0 || l == 0) return OS_OK;
@@ -205,8 +211,10 @@ extern "C" os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os
                                 : nullptr;
     void *lws = base + L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes;
     const float *cs = opts ? opts->col_scale : nullptr;
-    OSK_TRY(sketch_left_impl(p, A, a_t, m, lda, At, g, L.ldat, as, cs, lws, L.left_ws, st));
-    if (!sym) OSK_TRY(sketch_right_impl(p, B, b_t, l, ldb, BtT, g, L.ldbt, bs, st));
+    // Only the kept blocks are sketched: the dropped blocks' columns of A~ and
+    // B~ would never be read by the masked GEMM.
+    OSK_TRY(sketch_left_impl(p, A, a_t, m, lda, At, g, L.ldat, as, cs, mask, lws, L.left_ws, st));
+    if (!sym) OSK_TRY(sketch_right_impl(p, B, b_t, l, ldb, BtT, g, L.ldbt, bs, mask, lws, L.left_ws, st));
     int k = 0;
     for (int j = 0; j < p->P; ++j) k += (int)((mask >> j) & 1ull);
     return oversketch_gemm_masked(plan, At, L.ldat, as, BtT, L.ldbt, bs, g, m, l, mask, 1.0f / (float)k,

@@ -15,6 +15,10 @@ namespace osk {
 //   hs[j*n + i]   = h_j(i) | (sigma_j(i) < 0) << 31      (per-index lookup)
 //   perm[j*n + p] = i | (sigma_j(i) < 0) << 31           (bucket-sorted, i ascending in a bucket)
 //   offs[j*(b+1) + c] = start of bucket c of block j in perm[j*n ...]; offs[.. + b] = n
+//   pperm/poffs: the same lists with every bucket padded to a multiple of 4
+//   entries by kPadEntry (zero weight), so that the gather kernels can take
+//   members four at a time from one bucket; block j's list starts at
+//   pperm + j*pstride.
 struct Plan {
     int64_t n;
     int32_t b, N, e, P;
@@ -22,11 +26,15 @@ struct Plan {
     uint32_t *hs;
     uint32_t *perm;
     uint32_t *offs;
+    uint32_t *pperm;
+    uint32_t *poffs;
+    int64_t pstride;
     int device;
 };
 
 constexpr uint32_t kSignBit = 0x80000000u;
 constexpr uint32_t kIndexMask = 0x7fffffffu;
+constexpr uint32_t kPadEntry = 0x7fffffffu;   // padding entry: no index (n < 2^31 - 1)
 
 // Kept blocks of a mask as a list (launch parameter, passed by value).
 struct BlockList {

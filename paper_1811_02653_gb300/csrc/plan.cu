@@ -109,6 +109,35 @@ __global__ void chunk_scatter_kernel(const uint32_t *__restrict__ hs, int64_t n,
     }
 }
 
+// Padded bucket lists: poffs[j][c] = sum_{c' < c} roundup4(count(c')).
+__global__ void padded_offsets_kernel(const uint32_t *__restrict__ offs, int32_t b, int P,
+                                      uint32_t *__restrict__ poffs) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    uint32_t run = 0;
+    const uint32_t *o = offs + (int64_t)j * (b + 1);
+    for (int c = 0; c < b; ++c) {
+        poffs[(int64_t)j * (b + 1) + c] = run;
+        run += (o[c + 1] - o[c] + 3u) & ~3u;
+    }
+    poffs[(int64_t)j * (b + 1) + b] = run;
+}
+
+__global__ void padded_fill_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ offs,
+                                   const uint32_t *__restrict__ poffs, int64_t n, int32_t b, int P,
+                                   int64_t pstride, uint32_t *__restrict__ pperm) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)P * b) return;
+    const int j = (int)(t / b), c = (int)(t % b);
+    const uint32_t *o = offs + (int64_t)j * (b + 1);
+    const uint32_t *po = poffs + (int64_t)j * (b + 1);
+    const uint32_t cnt = o[c + 1] - o[c];
+    const uint32_t pcnt = po[c + 1] - po[c];
+    const uint32_t *src = perm + (int64_t)j * n + o[c];
+    uint32_t *dst = pperm + (int64_t)j * pstride + po[c];
+    for (uint32_t u = 0; u < pcnt; ++u) dst[u] = u < cnt ? src[u] : kPadEntry;
+}
+
 os_status check_params(int64_t n, int32_t b, int32_t N, int32_t e, oversketch_plan_t *out) {
     if (!out) return OS_ERR_INVALID_ARG;
     if (n < 1 || b < 1 || N < 1 || e < 0) return OS_ERR_INVALID_ARG;
@@ -123,6 +152,8 @@ void free_plan(Plan *p) {
     if (p->hs) cudaFree(p->hs);
     if (p->perm) cudaFree(p->perm);
     if (p->offs) cudaFree(p->offs);
+    if (p->pperm) cudaFree(p->pperm);
+    if (p->poffs) cudaFree(p->poffs);
     delete p;
 }
 
@@ -160,6 +191,11 @@ os_status build_csr(Plan *p, cudaStream_t st) {
         chunk_scatter_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(
             p->hs, n, b, P, (int)nchunks, chunk, cnt, p->offs, p->perm);
         if ((s = check_launch()) != OS_OK) break;
+        padded_offsets_kernel<<<1, 64, 0, st>>>(p->offs, b, P, p->poffs);
+        if ((s = check_launch()) != OS_OK) break;
+        padded_fill_kernel<<<(unsigned)(((int64_t)P * b + 127) / 128), 128, 0, st>>>(
+            p->perm, p->offs, p->poffs, n, b, P, p->pstride, p->pperm);
+        if ((s = check_launch()) != OS_OK) break;
         if (cudaStreamSynchronize(st) != cudaSuccess) { s = set_cuda_error(cudaGetLastError()); break; }
     } while (0);
     cudaFree(cnt);
@@ -175,11 +211,14 @@ os_status alloc_plan(int64_t n, int32_t b, int32_t N, int32_t e, uint64_t seed, 
     p->e = e;
     p->P = N + e;
     p->seed = seed;
-    p->hs = p->perm = p->offs = nullptr;
+    p->hs = p->perm = p->offs = p->pperm = p->poffs = nullptr;
+    p->pstride = (n + 3 * (int64_t)b + 3) / 4 * 4;
     cudaGetDevice(&p->device);
     const size_t tab = sizeof(uint32_t) * (size_t)p->P * n;
+    const size_t otab = sizeof(uint32_t) * (size_t)p->P * (b + 1);
     if (cudaMalloc(&p->hs, tab) != cudaSuccess || cudaMalloc(&p->perm, tab) != cudaSuccess ||
-        cudaMalloc(&p->offs, sizeof(uint32_t) * (size_t)p->P * (b + 1)) != cudaSuccess) {
+        cudaMalloc(&p->offs, otab) != cudaSuccess || cudaMalloc(&p->poffs, otab) != cudaSuccess ||
+        cudaMalloc(&p->pperm, sizeof(uint32_t) * (size_t)p->P * p->pstride) != cudaSuccess) {
         cudaGetLastError();
         free_plan(p);
         return OS_ERR_OOM;

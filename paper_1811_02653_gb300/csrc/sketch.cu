@@ -3,22 +3,31 @@
 //
 // One gather kernel serves both sides.  It reads a matrix X whose rows are
 // indexed by the sketched dimension i (n rows) and whose "free" dimension f
-// is contiguous in memory, and writes Y^T[f, q] for q = j*b + c:
+// runs along the other axis, and writes Y^T[f, q] for q = j*b + c:
 //
 //     Y^T[f, j*b + c] = sum_{i in bucket c of block j} sigma_j(i) * s_i * X[i, f]
 //
-// Right sketch: X = B (n x l), Y^T = B~^T (l x z).  Left sketch: X = A^T, staged
-// by a tiled transpose into the workspace, Y^T = A~ (m x z).
+// Right sketch: X = B (n x l), Y^T = B~^T (l x z).  Left sketch: X = A^T,
+// Y^T = A~ (m x z).
 //
-// A CTA owns 128 consecutive sketched columns q (whole buckets) and a strip of
-// 128 free indices.  Each warp walks the bucket-CSR of its buckets (indices
-// ascending inside a bucket, the same order in every run: no atomics, bitwise
-// reproducible) and gathers whole 128-wide row segments of X with 16-byte
-// loads, accumulating in FP32.  The 128 x 128 tile is transposed through
-// shared memory so that Y^T rows are written contiguously, and, for FP8, the
-// per-(row, 128-q) power-of-two scale is taken over exactly that row of the
-// tile.  CTAs of one strip are adjacent in launch order so the strip stays
-// in L2 while all of its buckets are gathered.
+// The operand is first packed strip-major into the workspace: strip s holds
+// X[0..n-1, 32s .. 32s+31] as n contiguous rows of 32 elements (zero-padded
+// past the free extent).  The bucket gather then reads random rows of one
+// 8 MB strip (for FP32, n = 65536) instead of 128-byte pieces of rows spread
+// over the whole matrix; on GB300 the latter runs at a quarter to a half of
+// the L2 gather rate because the translations of a matrix-wide random access
+// pattern do not stay cached.  Packing the left operand is the transpose it
+// needs anyway.
+//
+// A gather CTA owns 32 consecutive sketched columns q (whole buckets of one
+// block) and one strip.  Each warp walks the bucket-CSR of its buckets
+// (indices ascending inside a bucket, the same order in every run: no
+// atomics, bitwise reproducible) and gathers 128-byte row pieces with 16-byte
+// loads, accumulating in FP32.  The 32 x 32 tile is transposed through shared
+// memory so that Y^T rows are written contiguously.  FP8 output uses 128-column
+// tiles so that the per-(row, 128-q) power-of-two scale is taken inside one
+// CTA.  CTAs of one strip are adjacent in launch order, so a strip stays in L2
+// while all of its buckets are gathered.
 #include <cstdint>
 #include <cstdlib>
 #include <type_traits>
@@ -31,6 +40,7 @@ namespace {
 
 constexpr int kTileQ = 128;
 constexpr int kWarps = 8;
+constexpr int kStrip = 128;   // free indices per packed strip
 constexpr int kUnroll = 8;
 
 // VW consecutive elements of the free dimension per lane (strip = 32*VW).
@@ -71,114 +81,159 @@ __device__ __forceinline__ int fp8_scale_exponent(float amax) {
     return e < -127 ? -127 : (e > 127 ? 127 : e);
 }
 
+// Sixteen bytes of zeros: the row segment that padding entries of the bucket
+// lists point at, so the gather loop needs no predication.
+__device__ __align__(16) float g_zero_row[8];
+
 // Lane layout: lane = slot * 8 + sub.  The 4 slots of a warp gather 4
-// different members of the current bucket at once, each 8-lane group reading
-// a 32-element row segment (128 B for FP32) of X; lane `sub` holds elements
-// 4*sub .. 4*sub+3 of the strip.  Slot s accumulates members s, s+4, s+8, ...
-// in ascending order and the four partial sums are combined as
-// (p0 + p1) + (p2 + p3): a fixed order, so results are bitwise reproducible.
-template <typename InT, typename OutT, bool kAligned>
-__global__ void __launch_bounds__(kWarps * 32)
-sketch_gather_kernel(const InT *__restrict__ X, int64_t ldx, int64_t F,
-                     const uint32_t *__restrict__ perm, const uint32_t *__restrict__ offs,
-                     int64_t n, int32_t b, int32_t z, const float *__restrict__ col_scale,
+// different members of one bucket at once (bucket lists are padded to a
+// multiple of 4), each 8-lane group reading a 32-element row segment (128 B
+// for FP32) of X; lane `sub` holds elements 4*sub .. 4*sub+3 of the strip.
+// A warp owns QT/8 consecutive buckets and streams their (contiguous) padded
+// member list 32 entries at a time, keeping 8 independent 16-byte loads per
+// lane in flight and prefetching the next 32 entries.  Slot s accumulates
+// members s, s+4, s+8, ... of a bucket in ascending order and the four
+// partial sums are combined as (p0 + p1) + (p2 + p3): a fixed order, so the
+// results are bitwise reproducible.
+template <typename InT, typename OutT, int QT, bool kScale, int SLOTS>
+__global__ void __launch_bounds__(kWarps * 32, 4)
+sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ldx, int64_t F,
+                     const uint32_t *__restrict__ pperm, const uint32_t *__restrict__ poffs,
+                     int64_t pstride, int32_t b, int32_t z, const float *__restrict__ col_scale,
                      OutT *__restrict__ Yt, int64_t ldy, float *__restrict__ scales,
-                     int64_t lds) {
-    constexpr int TF = 32;               // free indices per CTA
+                     int64_t lds, BlockList blocks, int32_t tiles_per_block) {
+    constexpr int SUBS = 32 / SLOTS;     // lanes per member
+    constexpr int TF = 4 * SUBS;         // free indices per CTA (one strip)
     constexpr int PITCH = TF + 1;        // odd pitch: conflict-free column reads
-    constexpr int UNR = 4;               // groups of 4 members in flight per lane
-    __shared__ float tile[kTileQ * PITCH];
+    constexpr int G = 2 * SLOTS;         // groups of 4 members per batch: 8 loads per lane in flight
+    constexpr int QPW = QT / kWarps;     // buckets per warp
+    static_assert(QT == 32 || QT == 128, "tile of 32 or 128 sketched columns");
+    static_assert(SLOTS == 1 || SLOTS == 2 || SLOTS == 4, "1, 2 or 4 members per warp load");
+    extern __shared__ float4 smem_tile[];
+    float *tile = reinterpret_cast<float *>(smem_tile);   // [QT][PITCH]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = lane >> 3, sub = lane & 7;
-    const int q0 = blockIdx.x * kTileQ;
+    const int slot = lane / SUBS, sub = lane % SUBS;
+    // q0: first sketched column of this CTA, inside one of the listed blocks
+    const int bt = blockIdx.x / tiles_per_block;
+    const int jblk = blocks.idx[bt];
+    const int q0 = jblk * b + (blockIdx.x - bt * tiles_per_block) * QT;
+    const int qend = min(z, jblk * b + b);
     const int64_t f0 = (int64_t)blockIdx.y * TF;
-    const int64_t f = f0 + 4 * sub;
-    const bool full = kAligned && (f + 3 < F);
     using L = Loader<InT, 4, true>;
 
-    for (int t = 0; t < kTileQ / kWarps; ++t) {
-        const int qq = warp * (kTileQ / kWarps) + t;
-        const int q = q0 + qq;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        if (q < z) {
-            const int j = q / b, c = q - j * b;
-            const uint32_t *prow = perm + (int64_t)j * n;
-            const uint32_t beg = __ldg(offs + (int64_t)j * (b + 1) + c);
-            const uint32_t end = __ldg(offs + (int64_t)j * (b + 1) + c + 1);
-            for (uint32_t base = beg; base < end; base += 32) {
-                const int cnt = (int)min(32u, end - base);
-                const uint32_t my = lane < cnt ? __ldg(prow + base + lane) : 0u;
-                const float mysc = (col_scale && lane < cnt) ? __ldg(col_scale + (my & kIndexMask)) : 1.f;
-                for (int u = 0; u < cnt; u += 4 * UNR) {
-                    float v[UNR][4];
-                    float sg[UNR];
+    const int nb = min(QPW, qend - q0 - warp * QPW);   // buckets owned by this warp
+    if (nb > 0) {
+        const int cb = q0 - jblk * b + warp * QPW;        // first bucket (within the block)
+        const uint32_t *pl = pperm + (int64_t)jblk * pstride;
+        // group boundaries of the warp's buckets: lane t holds poffs[cb + t] / 4
+        const uint32_t gbl = lane <= nb ? __ldg(poffs + (int64_t)jblk * (b + 1) + cb + lane) >> 2 : 0u;
+        const uint32_t gend = __shfl_sync(0xffffffffu, gbl, nb);
+        // row i of the strip at xbase + i * row_bytes: one wide multiply-add per member
+        const uint64_t xbase = reinterpret_cast<uint64_t>(X + blockIdx.y * strip_stride + 4 * sub);
+        const uint32_t row_bytes = (uint32_t)(ldx * (int64_t)sizeof(InT));
+        const uint64_t zrow = reinterpret_cast<uint64_t>(g_zero_row);
+
+        // 32 entries starting at group g (past the warp's last group: padding)
+        auto load_entries = [&](uint32_t g) -> uint32_t {
+            const uint32_t pos = 4 * g + lane;
+            return pos < 4 * gend ? __ldg(pl + pos) : kPadEntry;
+        };
+        // GG groups (4*GG members) of the current bucket, entries in lanes 0 .. 4*GG-1 of e
+        auto batch = [&](auto gg, uint32_t e, float (&acc)[4]) {
+            constexpr int GG = decltype(gg)::value;
+            constexpr int KS = 4 * GG / SLOTS;            // member loads per lane
+            float sc_mine = 1.f;
+            if constexpr (kScale) sc_mine = e != kPadEntry ? __ldg(col_scale + (e & kIndexMask)) : 0.f;
+            float v[KS][4];
+            float wgt[KS];
 #pragma unroll
-                    for (int g = 0; g < UNR; ++g) {
-                        const int src = u + 4 * g + slot;
-                        const uint32_t ent = __shfl_sync(0xffffffffu, my, src & 31);
-                        const float sc = __shfl_sync(0xffffffffu, mysc, src & 31);
-                        const bool valid = src < cnt;
-                        sg[g] = valid ? ((ent & kSignBit) ? -sc : sc) : 0.f;
-                        const InT *ptr = X + (int64_t)(ent & kIndexMask) * ldx + f;
-                        if (valid && full) {
-                            L::load(ptr, v[g]);
-                        } else {
-#pragma unroll
-                            for (int w = 0; w < 4; ++w)
-                                v[g][w] = (valid && f + w < F) ? L::load1(ptr + w) : 0.f;
-                        }
-                    }
-#pragma unroll
-                    for (int g = 0; g < UNR; ++g)
-#pragma unroll
-                        for (int w = 0; w < 4; ++w) acc[w] = fmaf(sg[g], v[g][w], acc[w]);
+            for (int k = 0; k < KS; ++k) {
+                const uint32_t ent = __shfl_sync(0xffffffffu, e, k * SLOTS + slot);
+                // +-1 (or +-s_i) from the sign bit; padding reads the zero row
+                if constexpr (kScale) {
+                    const float sc = __shfl_sync(0xffffffffu, sc_mine, k * SLOTS + slot);
+                    wgt[k] = __uint_as_float(__float_as_uint(sc) ^ (ent & kSignBit));
+                } else {
+                    wgt[k] = __uint_as_float(0x3f800000u | (ent & kSignBit));
                 }
+                const uint64_t addr = (uint64_t)(ent & kIndexMask) * row_bytes + xbase;
+                L::load(reinterpret_cast<const InT *>(ent != kPadEntry ? addr : zrow), v[k]);
             }
-        }
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], 8);
-            acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], 16);
-        }
-        if (slot == 0) {
+            for (int k = 0; k < KS; ++k)
 #pragma unroll
-            for (int w = 0; w < 4; ++w) tile[qq * PITCH + 4 * sub + w] = acc[w];
+                for (int w = 0; w < 4; ++w) acc[w] = fmaf(wgt[k], v[k][w], acc[w]);
+        };
+        auto flush = [&](int t, float (&acc)[4]) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                if constexpr (SLOTS == 4) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], 8);
+                if constexpr (SLOTS >= 2) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], 16);
+            }
+            if (slot == 0) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) tile[(warp * QPW + t) * PITCH + 4 * sub + w] = acc[w];
+            }
+        };
+
+        // The warp's buckets are contiguous in the list: stream it in batches that
+        // never cross a bucket end (full batches of G groups, then the tail as
+        // G/2, G/4, ..., 1 groups), prefetching the next 32 entries each time.
+        uint32_t g = __shfl_sync(0xffffffffu, gbl, 0);
+        uint32_t e_cur = load_entries(g);
+        auto step = [&](auto gg, float (&acc)[4]) {
+            constexpr int GG = decltype(gg)::value;
+            const uint32_t e_nxt = load_entries(g + GG);
+            batch(gg, GG * 4 >= 32 ? e_cur : (lane < 4 * GG ? e_cur : kPadEntry), acc);
+            g += GG;
+            e_cur = e_nxt;
+        };
+        for (int t = 0; t < nb; ++t) {
+            const uint32_t gE = __shfl_sync(0xffffffffu, gbl, t + 1);
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            while (gE - g >= (uint32_t)G) step(std::integral_constant<int, G>(), acc);
+            const uint32_t r = gE - g;   // < G
+            if constexpr (G >= 8) if (r & 4u) step(std::integral_constant<int, 4>(), acc);
+            if constexpr (G >= 4) if (r & 2u) step(std::integral_constant<int, 2>(), acc);
+            if (r & 1u) step(std::integral_constant<int, 1>(), acc);
+            flush(t, acc);
         }
     }
     __syncthreads();
 
     // Transposed write-out: warp w writes rows f0 + 4w .. 4w+3 of Y^T.
+    constexpr int VPL = QT / 32;         // values per lane per row
     for (int t = 0; t < TF / kWarps; ++t) {
         const int ff = warp * (TF / kWarps) + t;
         const int64_t frow = f0 + ff;
         if (frow >= F) break;
-        float v[4];
+        float v[VPL];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = tile[(lane + 32 * k) * PITCH + ff];
+        for (int k = 0; k < VPL; ++k) v[k] = tile[(lane + 32 * k) * PITCH + ff];
         OutT *dst = Yt + frow * ldy + q0;
         if constexpr (sizeof(OutT) == 1) {
             float amax = 0.f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (q0 + lane + 32 * k < z) amax = fmaxf(amax, fabsf(v[k]));
+            for (int k = 0; k < VPL; ++k)
+                if (q0 + lane + 32 * k < qend) amax = fmaxf(amax, fabsf(v[k]));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
             const int e = fp8_scale_exponent(amax);
             const float inv = ldexpf(1.f, -e);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < VPL; ++k) {
                 const int q = q0 + lane + 32 * k;
-                if (q < z) {
+                if (q < qend) {
                     __nv_fp8_e4m3 r(v[k] * inv);   // RNE, saturating to +-448
                     dst[lane + 32 * k] = r;
                 }
             }
-            if (lane == 0) scales[frow * lds + q0 / kTileQ] = ldexpf(1.f, e);
+            if (lane == 0) scales[frow * lds + q0 / 128] = ldexpf(1.f, e);
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < VPL; ++k) {
                 const int q = q0 + lane + 32 * k;
-                if (q < z) {
+                if (q < qend) {
                     if constexpr (sizeof(OutT) == 4)
                         dst[lane + 32 * k] = v[k];
                     else
@@ -189,22 +244,76 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t ldx, int64_t F,
     }
 }
 
-// Tiled transpose: Xt[c, r] = X[r, c] (X rows x cols, ld ldx; Xt ld ldt).
-template <typename T>
-__global__ void __launch_bounds__(256) transpose_kernel(const T *__restrict__ X, int64_t ldx,
-                                                        int64_t rows, int64_t cols,
-                                                        T *__restrict__ Xt, int64_t ldt) {
-    __shared__ T tile[64][65];
-    const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;   // 64 x 4
-    for (int k = ty; k < 64; k += 4) {
-        const int64_t r = r0 + k, c = c0 + tx;
-        if (r < rows && c < cols) tile[k][tx] = X[r * ldx + c];
+// Strip-major packing of the right operand: Xs[s][i][t] = X[i, 128s + t]
+// (zero past the free extent F).  One thread moves 16 bytes; consecutive
+// threads read consecutive pieces of a row and write consecutive pieces of a
+// strip row.
+template <typename T, bool kVec>
+__global__ void __launch_bounds__(256) pack_rows_kernel(const T *__restrict__ X, int64_t ldx, int64_t n,
+                                                        int64_t F, int64_t nstrips, T *__restrict__ Xs) {
+    constexpr int V = 16 / sizeof(T);                // elements per 16-byte piece
+    constexpr int PPS = kStrip / V;                  // pieces per strip row
+    const int64_t pieces_per_row = nstrips * PPS;
+    const int64_t total = n * pieces_per_row;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / pieces_per_row;
+        const int64_t pr = t - i * pieces_per_row;
+        const int64_t s = pr / PPS, pc = pr - s * PPS;
+        const int64_t c0 = s * kStrip + pc * V;
+        uint4 u = make_uint4(0u, 0u, 0u, 0u);
+        if (kVec && c0 + V <= F) {
+            u = __ldg(reinterpret_cast<const uint4 *>(X + i * ldx + c0));
+        } else {
+            T *e = reinterpret_cast<T *>(&u);
+#pragma unroll
+            for (int k = 0; k < V; ++k) e[k] = c0 + k < F ? X[i * ldx + c0 + k] : T(0.f);
+        }
+        *reinterpret_cast<uint4 *>(Xs + (s * n + i) * kStrip + pc * V) = u;
+    }
+}
+
+// Strip-major packing of the left operand (a transpose): Xs[s][i][t] =
+// A[128s + t, i] (zero for rows past m).  A CTA moves a 32-row x 256-column
+// tile of A (a quarter of a strip's width) through shared memory with 16-byte
+// loads and stores; every strip row receives one contiguous 32-element piece.
+template <typename T, bool kVec>
+__global__ void __launch_bounds__(256) pack_cols_kernel(const T *__restrict__ A, int64_t lda, int64_t m,
+                                                        int64_t n, T *__restrict__ Xs) {
+    constexpr int W = 256;                          // columns of A per tile
+    constexpr int V = 16 / sizeof(T);               // elements per 16-byte vector
+    __shared__ T tile[32][W + 1];
+    const int64_t rb = blockIdx.y;                  // 32-row block of A
+    const int64_t s = rb / (kStrip / 32), quarter = rb % (kStrip / 32);
+    const int64_t i0 = (int64_t)blockIdx.x * W;
+    const int tid = threadIdx.x;
+    const bool whole = kVec && rb * 32 + 32 <= m && i0 + W <= n;
+    if (whole) {
+        for (int idx = tid; idx < 32 * W / V; idx += 256) {
+            const int r = idx / (W / V), cv = idx - r * (W / V);
+            const uint4 u = __ldg(reinterpret_cast<const uint4 *>(A + (rb * 32 + r) * lda + i0 + cv * V));
+            const T *e = reinterpret_cast<const T *>(&u);
+#pragma unroll
+            for (int k = 0; k < V; ++k) tile[r][cv * V + k] = e[k];
+        }
+    } else {
+        for (int idx = tid; idx < 32 * W; idx += 256) {
+            const int r = idx / W, c = idx - r * W;
+            const int64_t row = rb * 32 + r, col = i0 + c;
+            tile[r][c] = (row < m && col < n) ? A[row * lda + col] : T(0.f);
+        }
     }
     __syncthreads();
-    for (int k = ty; k < 64; k += 4) {
-        const int64_t c = c0 + k, r = r0 + tx;
-        if (r < rows && c < cols) Xt[c * ldt + r] = tile[tx][k];
+    // output: W strip rows, each receiving 32 elements (elements 32*quarter ..)
+    for (int idx = tid; idx < W * 32 / V; idx += 256) {
+        const int c = idx / (32 / V), rq = idx - c * (32 / V);
+        const int64_t col = i0 + c;
+        if (col >= n) continue;
+        uint4 u;
+        T *e = reinterpret_cast<T *>(&u);
+#pragma unroll
+        for (int k = 0; k < V; ++k) e[k] = tile[rq * V + k][c];
+        *reinterpret_cast<uint4 *>(Xs + (s * n + col) * kStrip + quarter * 32 + rq * V) = u;
     }
 }
 
@@ -260,37 +369,93 @@ __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     }
 }
 
-template <typename InT, typename OutT, bool kAligned>
-os_status launch_gather_t(const Plan *p, const InT *X, int64_t ldx, int64_t F, const float *col_scale,
-                          void *Yt, int64_t ldy, float *scales, cudaStream_t st) {
+template <typename InT, typename OutT, int QT, int SLOTS>
+os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int64_t ldx, int64_t F,
+                          const float *col_scale, void *Yt, int64_t ldy, float *scales,
+                          const BlockList &blocks, cudaStream_t st) {
     const int z = p->P * p->b;
-    dim3 grid((unsigned)((z + kTileQ - 1) / kTileQ), (unsigned)((F + 31) / 32));
+    const int tpb = (p->b + QT - 1) / QT;
+    constexpr int TF = 128 / SLOTS;
+    dim3 grid((unsigned)(tpb * blocks.count), (unsigned)((F + TF - 1) / TF));
     if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;
-    sketch_gather_kernel<InT, OutT, kAligned><<<grid, kWarps * 32, 0, st>>>(
-        X, ldx, F, p->perm, p->offs, p->n, p->b, z, col_scale, (OutT *)Yt, ldy, scales, z / kTileQ);
+    const size_t smem = sizeof(float) * QT * (TF + 1);
+    if (col_scale) {
+        auto k = sketch_gather_kernel<InT, OutT, QT, true, SLOTS>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
+                                          col_scale, (OutT *)Yt, ldy, scales, z / 128, blocks, tpb);
+    } else {
+        auto k = sketch_gather_kernel<InT, OutT, QT, false, SLOTS>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
+                                          nullptr, (OutT *)Yt, ldy, scales, z / 128, blocks, tpb);
+    }
     return check_launch();
 }
 
-template <typename InT, typename OutT>
-os_status launch_gather_o(const Plan *p, const InT *X, int64_t ldx, int64_t F, const float *col_scale,
-                          void *Yt, int64_t ldy, float *scales, cudaStream_t st) {
-    const bool aligned = aligned16(X) && (ldx * (int64_t)sizeof(InT)) % 16 == 0;
-    if (!aligned) return launch_gather_t<InT, OutT, false>(p, X, ldx, F, col_scale, Yt, ldy, scales, st);
-    return launch_gather_t<InT, OutT, true>(p, X, ldx, F, col_scale, Yt, ldy, scales, st);
-}
-
+// Gather from an operand packed in 128-wide strips (n rows each).  FP8 output
+// needs whole 128-column scale groups in one CTA; otherwise 32-column tiles
+// keep the CTAs that run together on few strips.
 template <typename InT>
-os_status launch_gather(const Plan *p, const InT *X, int64_t ldx, int64_t F, const float *col_scale,
-                        void *Yt, os_dtype out_t, int64_t ldy, float *scales, cudaStream_t st) {
+os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *col_scale, void *Yt,
+                        os_dtype out_t, int64_t ldy, float *scales, uint64_t block_mask, cudaStream_t st) {
+    const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
+    const int64_t ss = p->n * kStrip;
     switch (out_t) {
         case OS_F32:
-            return launch_gather_o<InT, float>(p, X, ldx, F, col_scale, Yt, ldy, scales, st);
+            return launch_gather_t<InT, float, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, blocks, st);
         case OS_BF16:
-            return launch_gather_o<InT, __nv_bfloat16>(p, X, ldx, F, col_scale, Yt, ldy, scales, st);
+            return launch_gather_t<InT, __nv_bfloat16, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales,
+                                                              blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_o<InT, __nv_fp8_e4m3>(p, X, ldx, F, col_scale, Yt, ldy, scales, st);
+            return launch_gather_t<InT, __nv_fp8_e4m3, 128, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales,
+                                                               blocks, st);
     }
     return OS_ERR_DTYPE;
+}
+
+// Gather straight from a row-major FP32 operand in 128-wide strips (512-byte row
+// pieces: one address translation per 512 bytes is cheap enough that no
+// packing pass is needed).  F must be a multiple of 128.
+os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, void *Yt, os_dtype out_t,
+                               int64_t ldy, float *scales, uint64_t block_mask, cudaStream_t st) {
+    const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
+    switch (out_t) {
+        case OS_F32:
+            return launch_gather_t<float, float, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, blocks, st);
+        case OS_BF16:
+            return launch_gather_t<float, __nv_bfloat16, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr,
+                                                                blocks, st);
+        case OS_FP8E4M3:
+            return launch_gather_t<float, __nv_fp8_e4m3, 128, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, scales,
+                                                                 blocks, st);
+    }
+    return OS_ERR_DTYPE;
+}
+
+template <typename T>
+os_status launch_pack_rows(const T *X, int64_t ldx, int64_t n, int64_t F, T *Xs, cudaStream_t st) {
+    const int64_t nstrips = (F + kStrip - 1) / kStrip;
+    const int64_t total = n * nstrips * (kStrip / (16 / (int64_t)sizeof(T)));
+    const int64_t blocks = (total + 255) / 256 < 152 * 64 ? (total + 255) / 256 : 152 * 64;
+    const bool vec = aligned16(X) && (ldx * (int64_t)sizeof(T)) % 16 == 0;
+    if (vec)
+        pack_rows_kernel<T, true><<<(unsigned)blocks, 256, 0, st>>>(X, ldx, n, F, nstrips, Xs);
+    else
+        pack_rows_kernel<T, false><<<(unsigned)blocks, 256, 0, st>>>(X, ldx, n, F, nstrips, Xs);
+    return check_launch();
+}
+
+template <typename T>
+os_status launch_pack_cols(const T *A, int64_t lda, int64_t m, int64_t n, T *Xs, cudaStream_t st) {
+    // 32-row blocks of the (zero-padded) strips
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + kStrip - 1) / kStrip * (kStrip / 32)));
+    if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;
+    if (aligned16(A) && (lda * (int64_t)sizeof(T)) % 16 == 0)
+        pack_cols_kernel<T, true><<<grid, 256, 0, st>>>(A, lda, m, n, Xs);
+    else
+        pack_cols_kernel<T, false><<<grid, 256, 0, st>>>(A, lda, m, n, Xs);
+    return check_launch();
 }
 
 os_status check_out(const Plan *p, int64_t rows, void *Yt, os_dtype out_t, int64_t ldy,
@@ -309,48 +474,71 @@ os_status check_out(const Plan *p, int64_t rows, void *Yt, os_dtype out_t, int64
 
 }  // namespace
 
-size_t left_workspace_bytes(const Plan *p, int64_t m, os_dtype a_t) {
-    const int64_t ldt = (m + 7) / 8 * 8;
-    return (size_t)p->n * ldt * dtype_size(a_t) + 256;
+// Packed-strip workspace for F free indices: ceil(F/128) strips of n x 128 elements.
+size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t) {
+    return (size_t)((F + kStrip - 1) / kStrip) * kStrip * (size_t)p->n * dtype_size(in_t) + 256;
 }
+
+namespace {
+void *ws_base(void *ws) {
+    return reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+}
+}  // namespace
 
 os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
-                           const float *col_scale, void *ws, size_t ws_bytes, cudaStream_t st) {
+                           const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
+                           cudaStream_t st) {
     if (!p || !A || m < 0) return OS_ERR_INVALID_ARG;
+    if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (a_t != OS_F32 && a_t != OS_BF16) return OS_ERR_DTYPE;
     if (lda < p->n) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_out(p, m, At, out_t, ldat, scales));
     if (m == 0) return OS_OK;
-    const size_t need = left_workspace_bytes(p, m, a_t);
-    if (!ws || ws_bytes < need) return OS_ERR_WORKSPACE;
-    const int64_t ldt = (m + 7) / 8 * 8;
-    void *Xt = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
-    dim3 tg((unsigned)((p->n + 63) / 64), (unsigned)((m + 63) / 64));
-    if (tg.y > 65535u) return OS_ERR_UNSUPPORTED;
+    if (!ws || ws_bytes < sketch_workspace_bytes(p, m, a_t)) return OS_ERR_WORKSPACE;
+    void *Xs = ws_base(ws);
     if (a_t == OS_F32) {
-        transpose_kernel<float><<<tg, 256, 0, st>>>((const float *)A, lda, m, p->n, (float *)Xt, ldt);
-        OSK_TRY(check_launch());
-        return launch_gather<float>(p, (const float *)Xt, ldt, m, col_scale, At, out_t, ldat, scales, st);
+        OSK_TRY(launch_pack_cols<float>((const float *)A, lda, m, p->n, (float *)Xs, st));
+        return launch_gather<float>(p, (const float *)Xs, m, col_scale, At, out_t, ldat, scales, block_mask, st);
     }
-    transpose_kernel<__nv_bfloat16><<<tg, 256, 0, st>>>((const __nv_bfloat16 *)A, lda, m, p->n,
-                                                       (__nv_bfloat16 *)Xt, ldt);
-    OSK_TRY(check_launch());
-    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xt, ldt, m, col_scale, At, out_t,
-                                        ldat, scales, st);
+    OSK_TRY(launch_pack_cols<__nv_bfloat16>((const __nv_bfloat16 *)A, lda, m, p->n, (__nv_bfloat16 *)Xs, st));
+    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, m, col_scale, At, out_t, ldat, scales,
+                                        block_mask, st);
 }
 
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
-                            void *BtT, os_dtype out_t, int64_t ldbt, float *scales, cudaStream_t st) {
+                            void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
+                            void *ws, size_t ws_bytes, cudaStream_t st) {
     if (!p || !B || l < 0) return OS_ERR_INVALID_ARG;
+    if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (b_t != OS_F32 && b_t != OS_BF16) return OS_ERR_DTYPE;
     if (ldb < l) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_out(p, l, BtT, out_t, ldbt, scales));
     if (l == 0) return OS_OK;
-    if (b_t == OS_F32)
-        return launch_gather<float>(p, (const float *)B, ldb, l, nullptr, BtT, out_t, ldbt, scales, st);
-    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)B, ldb, l, nullptr, BtT, out_t, ldbt,
-                                        scales, st);
+    // FP32 input with 16-byte aligned rows: gather whole 128-wide strips in place,
+    // and pack only a ragged remainder of fewer than 128 columns.
+    const bool direct = b_t == OS_F32 && aligned16(B) && ldb % 4 == 0 && ldb * 4 < (int64_t(1) << 32) &&
+                        l >= kStrip;
+    if (direct) {
+        const int64_t lf = l / kStrip * kStrip;
+        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, BtT, out_t, ldbt, scales, block_mask, st));
+        if (lf == l) return OS_OK;
+        if (!ws || ws_bytes < sketch_workspace_bytes(p, l - lf, b_t)) return OS_ERR_WORKSPACE;
+        float *Xs = (float *)ws_base(ws);
+        OSK_TRY(launch_pack_rows<float>((const float *)B + lf, ldb, p->n, l - lf, Xs, st));
+        char *yt = (char *)BtT + (size_t)lf * ldbt * dtype_size(out_t);
+        float *sc = scales ? scales + lf * ((int64_t)p->P * p->b / 128) : nullptr;
+        return launch_gather<float>(p, Xs, l - lf, nullptr, yt, out_t, ldbt, sc, block_mask, st);
+    }
+    if (!ws || ws_bytes < sketch_workspace_bytes(p, l, b_t)) return OS_ERR_WORKSPACE;
+    void *Xs = ws_base(ws);
+    if (b_t == OS_F32) {
+        OSK_TRY(launch_pack_rows<float>((const float *)B, ldb, p->n, l, (float *)Xs, st));
+        return launch_gather<float>(p, (const float *)Xs, l, nullptr, BtT, out_t, ldbt, scales, block_mask, st);
+    }
+    OSK_TRY(launch_pack_rows<__nv_bfloat16>((const __nv_bfloat16 *)B, ldb, p->n, l, (__nv_bfloat16 *)Xs, st));
+    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, l, nullptr, BtT, out_t, ldbt, scales,
+                                        block_mask, st);
 }
 
 os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t ldt, uint64_t mask,
@@ -396,28 +584,30 @@ os_status unsketch_rows_impl(const Plan *p, const float *U, int64_t l, int64_t l
 
 using namespace osk;
 
-extern "C" os_status oversketch_sketch_left_workspace(oversketch_plan_t plan, int64_t m,
-                                                      os_dtype a_t, size_t *bytes) {
+extern "C" os_status oversketch_sketch_workspace(oversketch_plan_t plan, int64_t free_extent,
+                                                 os_dtype in_t, size_t *bytes) {
     const Plan *p = reinterpret_cast<const Plan *>(plan);
-    if (!p || !bytes || m < 0) return OS_ERR_INVALID_ARG;
-    if (a_t != OS_F32 && a_t != OS_BF16) return OS_ERR_DTYPE;
-    *bytes = left_workspace_bytes(p, m, a_t);
+    if (!p || !bytes || free_extent < 0) return OS_ERR_INVALID_ARG;
+    if (in_t != OS_F32 && in_t != OS_BF16) return OS_ERR_DTYPE;
+    *bytes = sketch_workspace_bytes(p, free_extent, in_t);
     return OS_OK;
 }
 
 extern "C" os_status oversketch_sketch_left(oversketch_plan_t plan, const void *A, os_dtype a_t,
                                             int64_t m, int64_t lda, void *At, os_dtype out_t,
                                             int64_t ldat, float *scales, const float *col_scale,
-                                            void *workspace, size_t ws_bytes, void *stream) {
+                                            uint64_t block_mask, void *workspace, size_t ws_bytes,
+                                            void *stream) {
     return sketch_left_impl(reinterpret_cast<const Plan *>(plan), A, a_t, m, lda, At, out_t, ldat,
-                            scales, col_scale, workspace, ws_bytes, as_stream(stream));
+                            scales, col_scale, block_mask, workspace, ws_bytes, as_stream(stream));
 }
 
 extern "C" os_status oversketch_sketch_right(oversketch_plan_t plan, const void *B, os_dtype b_t,
                                              int64_t l, int64_t ldb, void *BtT, os_dtype out_t,
-                                             int64_t ldbt, float *scales, void *stream) {
+                                             int64_t ldbt, float *scales, uint64_t block_mask,
+                                             void *workspace, size_t ws_bytes, void *stream) {
     return sketch_right_impl(reinterpret_cast<const Plan *>(plan), B, b_t, l, ldb, BtT, out_t, ldbt,
-                             scales, as_stream(stream));
+                             scales, block_mask, workspace, ws_bytes, as_stream(stream));
 }
 
 extern "C" os_status oversketch_unsketch_cols(oversketch_plan_t plan, const float *T, int64_t m,

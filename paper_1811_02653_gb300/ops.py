@@ -61,12 +61,12 @@ def load_library(path: str | None = None):
             "oversketch_plan_get_tables": (st, [vp, vp, vp, vp, vp]),
             "oversketch_plan_info": (st, [vp, vp, vp, vp, vp]),
             "oversketch_plan_destroy": (st, [vp]),
-            "oversketch_sketch_left_workspace": (st, [vp, i64, st, ctypes.POINTER(sz)]),
-            "oversketch_sketch_left": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, vp, sz, vp]),
-            "oversketch_sketch_right": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp]),
+            "oversketch_sketch_workspace": (st, [vp, i64, st, ctypes.POINTER(sz)]),
+            "oversketch_sketch_left": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, u64, vp, sz, vp]),
+            "oversketch_sketch_right": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, u64, vp, sz, vp]),
             "oversketch_gemm_masked": (st, [vp, vp, i64, vp, vp, i64, vp, st, i64, i64, u64, f32, f32,
                                             vp, i64, vp]),
-            "oversketch_workspace_size": (st, [vp, i64, i64, st, ctypes.POINTER(_Opts), ctypes.POINTER(sz)]),
+            "oversketch_workspace_size": (st, [vp, i64, i64, st, st, ctypes.POINTER(_Opts), ctypes.POINTER(sz)]),
             "oversketch_matmul": (st, [vp, vp, st, i64, vp, st, i64, vp, i64, i64, i64, i64, u64,
                                        ctypes.POINTER(_Opts), vp, sz, vp]),
             "oversketch_unsketch_cols": (st, [vp, vp, i64, i64, u64, f32, vp, st, i64, vp]),
@@ -89,7 +89,7 @@ def exported_symbols() -> list[str]:
 def _sigs_names():
     return ["oversketch_status_string", "oversketch_last_cuda_error", "oversketch_plan",
             "oversketch_plan_from_tables", "oversketch_plan_get_tables", "oversketch_plan_info",
-            "oversketch_plan_destroy", "oversketch_sketch_left_workspace", "oversketch_sketch_left",
+            "oversketch_plan_destroy", "oversketch_sketch_workspace", "oversketch_sketch_left",
             "oversketch_sketch_right", "oversketch_gemm_masked", "oversketch_workspace_size",
             "oversketch_matmul", "oversketch_unsketch_cols", "oversketch_unsketch_rows",
             "oversketch_frob", "oversketch_device_status"]
@@ -207,16 +207,22 @@ def _fp8_scales_shape(rows, z):
     return (rows, (z + 127) // 128)
 
 
-def sketch_left_workspace(p: Plan, m: int, a_dtype=torch.float32) -> int:
+def sketch_workspace(p: Plan, free_extent: int, in_dtype=torch.float32) -> int:
+    """Bytes of the packed-strip workspace for a sketch with this free extent."""
     out = ctypes.c_size_t()
-    _check(load_library().oversketch_sketch_left_workspace(p.handle, m, _dtype_code(a_dtype),
-                                                           ctypes.byref(out)),
-           "oversketch_sketch_left_workspace")
+    _check(load_library().oversketch_sketch_workspace(p.handle, free_extent, _dtype_code(in_dtype),
+                                                      ctypes.byref(out)), "oversketch_sketch_workspace")
     return out.value
 
 
+def _workspace(p, F, dtype, device, workspace):
+    if workspace is None:
+        workspace = torch.empty(sketch_workspace(p, F, dtype), dtype=torch.uint8, device=device)
+    return workspace
+
+
 def sketch_left(p: Plan, A: torch.Tensor, out_dtype="f32", col_scale=None, out=None,
-                scales=None, workspace=None, stream=None):
+                scales=None, workspace=None, block_mask=0, stream=None):
     """A~ = A diag(col_scale) S (m x z, K-major); returns (At, scales or None)."""
     lda = _rowmajor(A, "A")
     m = A.shape[0]
@@ -226,15 +232,16 @@ def sketch_left(p: Plan, A: torch.Tensor, out_dtype="f32", col_scale=None, out=N
         out = torch.empty((m, ld), dtype=_TORCH_DT[od], device=A.device)[:, :p.z]
     if od == FP8 and scales is None:
         scales = torch.empty(_fp8_scales_shape(m, p.z), dtype=torch.float32, device=A.device)
-    if workspace is None:
-        workspace = torch.empty(sketch_left_workspace(p, m, A.dtype), dtype=torch.uint8, device=A.device)
+    workspace = _workspace(p, m, A.dtype, A.device, workspace)
     _check(load_library().oversketch_sketch_left(
         p.handle, _ptr(A), _dt(A), m, lda, _ptr(out), od, out.stride(0), _ptr(scales),
-        _ptr(col_scale), _ptr(workspace), workspace.numel(), _stream(stream)), "oversketch_sketch_left")
+        _ptr(col_scale), block_mask, _ptr(workspace), workspace.numel(), _stream(stream)),
+        "oversketch_sketch_left")
     return out, scales
 
 
-def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=None, stream=None):
+def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=None, block_mask=0,
+                 workspace=None, stream=None):
     """B~^T = (S^T B)^T (l x z, K-major); returns (BtT, scales or None)."""
     ldb = _rowmajor(B, "B")
     l = B.shape[1]
@@ -244,9 +251,10 @@ def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=Non
         out = torch.empty((l, ld), dtype=_TORCH_DT[od], device=B.device)[:, :p.z]
     if od == FP8 and scales is None:
         scales = torch.empty(_fp8_scales_shape(l, p.z), dtype=torch.float32, device=B.device)
+    workspace = _workspace(p, l, B.dtype, B.device, workspace)
     _check(load_library().oversketch_sketch_right(
-        p.handle, _ptr(B), _dt(B), l, ldb, _ptr(out), od, out.stride(0), _ptr(scales), _stream(stream)),
-        "oversketch_sketch_right")
+        p.handle, _ptr(B), _dt(B), l, ldb, _ptr(out), od, out.stride(0), _ptr(scales), block_mask,
+        _ptr(workspace), workspace.numel(), _stream(stream)), "oversketch_sketch_right")
     return out, scales
 
 
@@ -270,11 +278,12 @@ def _opts(gemm_dtype, col_scale=None, symmetric=False):
 
 
 def workspace_size(p: Plan, m: int, l: int, a_dtype=torch.float32, gemm_dtype="f32",
-                   symmetric=False) -> int:
+                   symmetric=False, b_dtype=torch.float32) -> int:
     out = ctypes.c_size_t()
     o = _opts(gemm_dtype, None, symmetric)
     _check(load_library().oversketch_workspace_size(p.handle, m, l, _dtype_code(a_dtype),
-                                                    ctypes.byref(o), ctypes.byref(out)),
+                                                    _dtype_code(b_dtype), ctypes.byref(o),
+                                                    ctypes.byref(out)),
            "oversketch_workspace_size")
     return out.value
 
@@ -293,7 +302,8 @@ def matmul(p: Plan, A, B, mask: int, gemm_dtype="f32", col_scale=None, symmetric
         C = torch.empty((m, l), dtype=torch.float32, device=A.device)
     o = _opts(gemm_dtype, col_scale, symmetric)
     if workspace is None:
-        workspace = torch.empty(workspace_size(p, m, l, A.dtype, gemm_dtype, symmetric),
+        workspace = torch.empty(workspace_size(p, m, l, A.dtype, gemm_dtype, symmetric,
+                                               B.dtype if B is not None else torch.float32),
                                 dtype=torch.uint8, device=A.device)
     _check(load_library().oversketch_matmul(
         p.handle, _ptr(A), _dt(A), lda, bp, bt, ldb, _ptr(C), C.stride(0), m, n, l, mask,

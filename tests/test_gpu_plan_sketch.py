@@ -82,6 +82,8 @@ SKETCH_CASES = [
     (300, 2000, 130, 128, 3, 2),       # ragged tiles, free dims not multiples of 128
     (7, 513, 5, 32, 2, 1),             # tiny, odd sizes
     (129, 4096, 257, 1024, 2, 1),      # one bucket per CTA tile row
+    (64, 3000, 300, 128, 3, 1),        # right sketch: 128-wide strips in place + packed remainder
+    (32, 2048, 384, 256, 2, 1),        # right sketch: whole 128-wide strips only
 ]
 
 
@@ -207,3 +209,28 @@ def test_frob_fp64(ops):
     out1 = ops.frob(_dev(X)).cpu().numpy()
     assert np.isclose(out1[0], (X64 ** 2).sum(), rtol=1e-12)
     assert np.array_equal(out, ops.frob(_dev(X), _dev(Y)).cpu().numpy())
+
+
+def test_sketch_block_mask(ops):
+    # only the listed blocks are computed; other columns are left untouched
+    m, n, l, b, N, e = 96, 3000, 70, 128, 4, 1
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    B = rng.standard_normal((n, l)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 4)
+    h, s = oracle.hash_tables(n, b, N, e, 4)
+    mask = 0b10110
+    At = torch.full((m, p.z), 7.0, device="cuda")
+    BtT = torch.full((l, p.z), 7.0, device="cuda")
+    ops.sketch_left(p, _dev(A), "f32", out=At, block_mask=mask)
+    ops.sketch_right(p, _dev(B), "f32", out=BtT, block_mask=mask)
+    ref_l, bd_l = sketch_bounds_left(A, h, s, b)
+    ref_r, bd_r = sketch_bounds_right(B, h, s, b)
+    cols = oracle.selected_columns(mask, N + e, b)
+    other = np.setdiff1d(np.arange(p.z), cols)
+    At_h, Bt_h = At.cpu().numpy(), BtT.cpu().numpy()
+    assert_fp32_within(At_h[:, cols], ref_l[:, cols], bd_l[:, cols])
+    assert_fp32_within(Bt_h[:, cols], ref_r.T[:, cols], bd_r.T[:, cols])
+    assert (At_h[:, other] == 7.0).all() and (Bt_h[:, other] == 7.0).all()
+    with pytest.raises(ops.OverSketchError, match="MASK"):
+        ops.sketch_left(p, _dev(A), "f32", block_mask=1 << 5)
