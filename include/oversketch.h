@@ -158,6 +158,33 @@ OS_API os_status oversketch_sketch_right(oversketch_plan_t plan, const void *B, 
                                   size_t ws_bytes, void *stream);
 
 /* -------------------------------------------------------------------------
+ * Left sketch without allocation.  The paper has no counterpart: this is a
+ * library convenience.  Same operation, arguments and errors as
+ * oversketch_sketch_left, but the packing workspace is a fixed scratch array
+ * of 32 MiB in device memory that every GPU loading the library holds until
+ * the process exits.  For callers that cannot allocate device memory at the
+ * point where they sketch: code running while a stream is captured into a
+ * CUDA graph (cudaMalloc is not permitted there), code whose memory belongs to
+ * another allocator or a fixed budget, and latency-critical loops that must
+ * not call cudaMalloc (it can synchronise the device).  The call allocates
+ * nothing; the plan and the output are the caller's.
+ *   - Limit: oversketch_sketch_workspace(plan, m, a_t) <= 32 MiB (for FP32
+ *     that is ceil(m/128) * 128 * n * 4 bytes), else OS_ERR_WORKSPACE and no
+ *     launch.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; every
+ *     byte a call reads is written by that call first, so nothing needs
+ *     clearing.  Calls that overlap on the GPU (different streams, or several
+ *     threads) race on the array: serialise them.
+ */
+OS_API os_status oversketch_sketch_left_noalloc(oversketch_plan_t plan, const void *A, os_dtype a_t,
+                                         int64_t m, int64_t lda, void *At, os_dtype out_t,
+                                         int64_t ldat, float *scales, const float *col_scale,
+                                         uint64_t block_mask, void *stream);
+
+/* -------------------------------------------------------------------------
  * Masked block-sum GEMM (Alg. 3 computation + termination + reduction; the
  * b x b block products of Alg. 2 become one GEMM whose inner dimension is
  * the concatenation of the kept blocks):

@@ -73,6 +73,7 @@ def load_library(path: str | None = None):
             "oversketch_unsketch_rows": (st, [vp, vp, i64, i64, u64, f32, vp, st, i64, vp]),
             "oversketch_frob": (st, [vp, i64, vp, i64, i64, i64, vp, vp, sz, vp]),
             "oversketch_device_status": (st, [vp, ctypes.POINTER(i32), i32]),
+            "oversketch_sketch_left_noalloc": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, u64, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -92,7 +93,7 @@ def _sigs_names():
             "oversketch_plan_destroy", "oversketch_sketch_workspace", "oversketch_sketch_left",
             "oversketch_sketch_right", "oversketch_gemm_masked", "oversketch_workspace_size",
             "oversketch_matmul", "oversketch_unsketch_cols", "oversketch_unsketch_rows",
-            "oversketch_frob", "oversketch_device_status"]
+            "oversketch_frob", "oversketch_device_status", "oversketch_sketch_left_noalloc"]
 
 
 def _check(status: int, what: str):
@@ -349,3 +350,17 @@ def device_status(reset=True, stream=None) -> int:
     _check(load_library().oversketch_device_status(_stream(stream), ctypes.byref(out), 1 if reset else 0),
            "oversketch_device_status")
     return out.value
+
+
+def sketch_left_noalloc(p: Plan, A: torch.Tensor, out: torch.Tensor, out_dtype="f32", col_scale=None,
+                        scales=None, block_mask=0, stream=None):
+    """A~ into the caller's `out` using the library's fixed 32 MiB scratch array
+    instead of a workspace: for callers that cannot allocate device memory.
+    Raises OverSketchError (OS_ERR_WORKSPACE) when the packed operand does not
+    fit."""
+    lda = _rowmajor(A, "A")
+    od = _dtype_code(out_dtype)
+    _check(load_library().oversketch_sketch_left_noalloc(
+        p.handle, _ptr(A), _dt(A), A.shape[0], lda, _ptr(out), od, out.stride(0), _ptr(scales),
+        _ptr(col_scale), block_mask, _stream(stream)), "oversketch_sketch_left_noalloc")
+    return out
