@@ -303,6 +303,32 @@ def run_ours(args):
     h2d = A_h.numel() * 4 + B_h.numel() * 4
     d2h = C_h.numel() * 4
 
+    # ---- exact GEMM on the same GPU: the same tcgen05 kernel over K = n (all blocks kept) ----
+    exact = None
+    if not args.no_exact and w.n % 64 == 0 and w.n // 64 <= 4096:
+        bx = 1024 if w.n % 1024 == 0 and w.n // 1024 <= 64 else None
+        if bx is not None:
+            A16 = A.to(torch.bfloat16)
+            Bt16 = B.t().contiguous().to(torch.bfloat16)         # l x n, K-major (setup, untimed)
+            pe = ops.plan(w.n, bx, w.n // bx, 0, 0)
+            full = (1 << (w.n // bx)) - 1
+            Cx = torch.empty((w.m, w.l), dtype=torch.float32, device=dev)
+            ops.gemm_masked(pe, A16, Bt16, full, alpha=1.0, C=Cx)
+            torch.cuda.synchronize()
+            x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            x0.record(stream)
+            for _ in range(reps):
+                ops.gemm_masked(pe, A16, Bt16, full, alpha=1.0, C=Cx)
+            x1.record(stream)
+            torch.cuda.synchronize()
+            ex_ms = x0.elapsed_time(x1) / reps
+            exact = {"ms": ex_ms, "tflops": flop_eff / (ex_ms * 1e-3) / 1e12, "dtype": "bf16",
+                     "kernel": "gemm_masked_bf16_kernel with every block of a width-1024 split of n kept",
+                     "sketched_speedup": ex_ms / ms}
+            exact_C = Cx
+            del A16, Bt16
+
     # ---- dominant kernel and its roofline ----
     es = {"bf16": 2, "f32": 4, "fp8": 1}[gd]
     n_kept = w.k
@@ -323,8 +349,13 @@ def run_ours(args):
         peak = peaks.get("hbm_gbs")
         bound, unit, ach = "hbm", "GB/s", right_bytes / (t_right * 1e-3) / 1e9
         per_launch = {"bytes": right_bytes}
+    # DRAM bytes per launch from one ncu capture of this command (profiles/square_launch_list.md);
+    # valid for the square workload with the kernels as they were when captured
+    traffic = None
+    if dom == "gemm_masked_bf16_kernel" and (w.m, w.n, w.l) == (16384, 65536, 16384):
+        traffic = 3755223808 + 1052628480
     roof = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-            "frac": (ach / peak) if peak else None, "traffic": None, "kernel": dom,
+            "frac": (ach / peak) if peak else None, "traffic": traffic, "kernel": dom,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
             "algorithmic_per_launch": per_launch}
 
@@ -348,6 +379,8 @@ def run_ours(args):
         ops.matmul(p, A, B, w.mask, gd, C=C, workspace=ws_mm)
         C_s = C[rows][:, cols].cpu().numpy().astype(np.float64)
         AB = Ar @ Bc
+        if exact is not None:
+            exact["vs_exact_rel_frob"] = oracle.rel_frob(exact_C[rows][:, cols].cpu().numpy(), Ar @ Bc)
         err = {"vs_oracle_rel_frob": oracle.rel_frob(C_s, C_or),
                "vs_exact_rel_frob": oracle.rel_frob(C_s, AB),
                "oracle_sketch_vs_exact_rel_frob": oracle.rel_frob(C_or_exact_sketch, AB),
@@ -366,7 +399,7 @@ def run_ours(args):
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * flop_eff / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 5 * args.steps, "clocks": clk, "error": err}
+            "gpu_launches": 4 * args.steps, "clocks": clk, "error": err, "exact_gemm": exact}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -385,6 +418,7 @@ def main():
     ap.add_argument("--shape", default="", help="m,n,l override for profiling captures")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-exact", action="store_true", help="skip the exact-GEMM comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
