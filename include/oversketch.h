@@ -224,13 +224,15 @@ OS_API os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os_dty
 
 /* -------------------------------------------------------------------------
  * Adjoints of the sketch restricted to the kept blocks (the backward pass of
- * (*) as a function of A and B):
- *   unsketch_cols: dX[r, i] = scale * sum_{j in mask} sigma_j(i) T[r, j*b + h_j(i)]
- *                  T: m x z FP32 (ldt); dX: m x n in dtype x_t (ldx).
- *   unsketch_rows: dG[i, c] = scale * sum_{j in mask} sigma_j(i) U[j*b + h_j(i), c]
- *                  U: z x l FP32 (ldu); dG: n x l in dtype g_t (ldg).
- * x_t / g_t: OS_F32 or OS_BF16.  Errors: OS_ERR_MASK, OS_ERR_INVALID_ARG,
- * OS_ERR_DTYPE, OS_ERR_CUDA.
+ * (*) as a function of A and B; S_sel is S of Eq. 3 restricted to the kept
+ * blocks).  The inputs hold the kept blocks only, compacted in ascending
+ * block order (column / row t*b + c belongs to the t-th kept block):
+ *   unsketch_cols: dX[r, i] = scale * sum_t sigma_j(i) T[r, t*b + h_j(i)],  j = kept[t]
+ *                  T: m x (k*b) FP32 (ldt); dX: m x n in dtype x_t (ldx).
+ *   unsketch_rows: dG[i, c] = scale * sum_t sigma_j(i) U[t*b + h_j(i), c],  j = kept[t]
+ *                  U: (k*b) x l FP32 (ldu); dG: n x l in dtype g_t (ldg).
+ * x_t / g_t: OS_F32 or OS_BF16.  Sums in FP32 over kept blocks in ascending
+ * order.  Errors: OS_ERR_MASK, OS_ERR_INVALID_ARG, OS_ERR_DTYPE, OS_ERR_CUDA.
  */
 OS_API os_status oversketch_unsketch_cols(oversketch_plan_t plan, const float *T, int64_t m, int64_t ldt,
                                    uint64_t mask, float scale, void *dX, os_dtype x_t,
@@ -238,6 +240,31 @@ OS_API os_status oversketch_unsketch_cols(oversketch_plan_t plan, const float *T
 OS_API os_status oversketch_unsketch_rows(oversketch_plan_t plan, const float *U, int64_t l,
                                    int64_t ldu, uint64_t mask, float scale, void *dG,
                                    os_dtype g_t, int64_t ldg, void *stream);
+
+/* -------------------------------------------------------------------------
+ * Plain BF16 GEMM on the tensor cores (the same tcgen05 kernel with one K
+ * block), used by the backward pass:
+ *   C = alpha * A . B^T (+ beta * C),  A: m x K, B: n x K, both K-major BF16
+ *   (16-byte aligned rows, so K % 8 == 0 when lda == K), C: m x n FP32.
+ */
+OS_API os_status oversketch_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m,
+                               int64_t n, int64_t K, float alpha, float beta, float *C, int64_t ldc,
+                               void *stream);
+
+/* -------------------------------------------------------------------------
+ * Layout conversions (data movement only):
+ *   select_transpose: Y[c', r] = X[r, col(c')] for an X of rows x cols (ldx);
+ *     block_mask == 0: all columns (col(c') = c'); else the columns of the
+ *     blocks of width b whose bits are set, compacted in ascending order
+ *     (cols % b == 0, cols / b <= 64).  Y: (selected cols) x rows (ldy).
+ *   cast: Y = X elementwise, rows x cols.
+ * x_t, y_t: OS_F32 or OS_BF16 (FP32 -> BF16 rounds to nearest even).
+ */
+OS_API os_status oversketch_select_transpose(const void *X, os_dtype x_t, int64_t rows, int64_t cols,
+                                      int64_t ldx, uint64_t block_mask, int32_t b, void *Y,
+                                      os_dtype y_t, int64_t ldy, void *stream);
+OS_API os_status oversketch_cast(const void *X, os_dtype x_t, int64_t rows, int64_t cols, int64_t ldx,
+                          void *Y, os_dtype y_t, int64_t ldy, void *stream);
 
 /* -------------------------------------------------------------------------
  * FP64 error measurement (Def. 4.1 is stated in squared Frobenius norms):

@@ -286,24 +286,23 @@ int num_sms() {
 
 }  // namespace
 
-os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const float *a_scales,
-                         const void *BtT, int64_t ldbt, const float *b_scales, os_dtype dt, int64_t m,
-                         int64_t l, uint64_t mask, float alpha, float beta, float *C, int64_t ldc,
-                         cudaStream_t st) {
-    (void)a_scales;
-    (void)b_scales;
-    if (dt != OS_BF16) return OS_ERR_UNSUPPORTED;
-    if (p->b % BK != 0) return OS_ERR_UNSUPPORTED;
-    if (!aligned16(At) || !aligned16(BtT) || (ldat * 2) % 16 != 0 || (ldbt * 2) % 16 != 0)
-        return OS_ERR_INVALID_ARG;
-    const int64_t z = (int64_t)p->P * p->b;
+namespace {
+
+// C = alpha * sum over the listed K blocks of A_blk . B_blk^T (+ beta C); A rows x zK
+// and B cols x zK are K-major BF16 with zK columns in total.
+os_status launch_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l,
+                      int64_t zK, int32_t blk, const BlockList &kept, float alpha, float beta, float *C,
+                      int64_t ldc, cudaStream_t st) {
+    if (blk % BK != 0) return OS_ERR_UNSUPPORTED;
+    if (!aligned16(A) || !aligned16(B) || (lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0) return OS_ERR_INVALID_ARG;
+    if (zK >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
     GemmArgs g;
     g.m = m;
     g.l = l;
-    g.b = p->b;
-    g.kb_per_blk = p->b / BK;
-    g.kept = mask_to_list(mask, p->P);
-    g.num_kb = g.kept.count * g.kb_per_blk;
+    g.b = blk;
+    g.kb_per_blk = blk / BK;
+    g.kept = kept;
+    g.num_kb = kept.count * g.kb_per_blk;
     g.tiles_m = (int)((m + BM - 1) / BM);
     g.tiles_n = (int)((l + BN - 1) / BN);
     g.num_tiles = g.tiles_m * g.tiles_n;
@@ -312,8 +311,8 @@ os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const floa
     g.C = C;
     g.ldc = ldc;
     CUtensorMap ta, tb;
-    OSK_TRY(make_tmap(&ta, At, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, z, ldat, BM, BK));
-    OSK_TRY(make_tmap(&tb, BtT, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, z, ldbt, BN, BK));
+    OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, zK, lda, BM, BK));
+    OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, zK, ldb, BN, BK));
     static bool attr_set = false;
     if (!attr_set) {
         OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_masked_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -323,6 +322,19 @@ os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const floa
     const int grid = g.num_tiles < num_sms() ? g.num_tiles : num_sms();
     gemm_masked_bf16_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, g);
     return check_launch();
+}
+
+}  // namespace
+
+os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const float *a_scales,
+                         const void *BtT, int64_t ldbt, const float *b_scales, os_dtype dt, int64_t m,
+                         int64_t l, uint64_t mask, float alpha, float beta, float *C, int64_t ldc,
+                         cudaStream_t st) {
+    (void)a_scales;
+    (void)b_scales;
+    if (dt != OS_BF16) return OS_ERR_UNSUPPORTED;
+    return launch_bf16(At, ldat, BtT, ldbt, m, l, (int64_t)p->P * p->b, p->b, mask_to_list(mask, p->P), alpha,
+                       beta, C, ldc, st);
 }
 
 }  // namespace osk
@@ -342,4 +354,18 @@ extern "C" os_status oversketch_device_status(void *stream, int32_t *status, int
         OSK_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return OS_OK;
+}
+
+extern "C" os_status oversketch_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m,
+                                          int64_t n, int64_t K, float alpha, float beta, float *C, int64_t ldc,
+                                          void *stream) {
+    if (!A || !B || !C || m < 0 || n < 0 || K < 0 || ldc < n || lda < K || ldb < K) return OS_ERR_INVALID_ARG;
+    if (m == 0 || n == 0) return OS_OK;
+    if (K == 0) return OS_ERR_UNSUPPORTED;
+    // one K block rounded up to the 64-wide K tile; TMA fills the columns past K with zeros
+    BlockList one;
+    one.count = 1;
+    for (int t = 0; t < 64; ++t) one.idx[t] = 0;
+    const int64_t kpad = (K + 63) / 64 * 64;
+    return launch_bf16(A, lda, B, ldb, m, n, K, (int32_t)kpad, one, alpha, beta, C, ldc, as_stream(stream));
 }

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const T *__restrict__ A,
     }
 }
 
-// dX[r, i] = scale * sum_{j kept} sigma_j(i) T[r, j*b + h_j(i)]
+// dX[r, i] = scale * sum_{t < k} sigma_j(i) T[r, t*b + h_j(i)], j = kept[t]  (T holds the kept blocks only)
 template <typename OutT>
 __global__ void __launch_bounds__(256) unsketch_cols_kernel(
     const float *__restrict__ T, int64_t m, int64_t ldt, const uint32_t *__restrict__ hs, int64_t n,
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) unsketch_cols_kernel(
         for (int t = 0; t < kept.count; ++t) {
             const int j = kept.idx[t];
             const uint32_t v = __ldg(hs + (int64_t)j * n + i);
-            const float x = __ldg(trow + (int64_t)j * b + (v & kIndexMask));
+            const float x = __ldg(trow + (int64_t)t * b + (v & kIndexMask));   // kept blocks compacted
             acc += (v & kSignBit) ? -x : x;
         }
         acc *= scale;
@@ -341,8 +341,8 @@ __global__ void __launch_bounds__(256) unsketch_cols_kernel(
     }
 }
 
-// dG[i, c] = scale * sum_{j kept} sigma_j(i) U[j*b + h_j(i), c]; one warp per
-// row i, whole-row gathers of U.
+// dG[i, c] = scale * sum_{t < k} sigma_j(i) U[t*b + h_j(i), c], j = kept[t] (U holds
+// the kept blocks only); one warp per row i, whole-row gathers of U.
 template <typename OutT>
 __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     const float *__restrict__ U, int64_t l, int64_t ldu, const uint32_t *__restrict__ hs, int64_t n,
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     for (int t = 0; t < kept.count; ++t) {
         const int j = kept.idx[t];
         const uint32_t v = __ldg(hs + (int64_t)j * n + i);
-        rows[t] = (int64_t)j * b + (v & kIndexMask);
+        rows[t] = (int64_t)t * b + (v & kIndexMask);                          // kept blocks compacted
         sg[t] = (v & kSignBit) ? -scale : scale;
     }
     for (int64_t c = c0 + lane; c < min(l, c0 + 1024); c += 32) {
@@ -545,7 +545,8 @@ os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t l
                              float scale, void *dX, os_dtype x_t, int64_t ldx, cudaStream_t st) {
     if (!p || !T || !dX || m < 0) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_mask(mask, p->P));
-    if (ldt < (int64_t)p->P * p->b || ldx < p->n) return OS_ERR_INVALID_ARG;
+    const int kcnt = __builtin_popcountll(mask);
+    if (ldt < (int64_t)kcnt * p->b || ldx < p->n) return OS_ERR_INVALID_ARG;
     if (x_t != OS_F32 && x_t != OS_BF16) return OS_ERR_DTYPE;
     if (m == 0) return OS_OK;
     if (m > 65535) return OS_ERR_UNSUPPORTED;

@@ -74,6 +74,9 @@ def load_library(path: str | None = None):
             "oversketch_frob": (st, [vp, i64, vp, i64, i64, i64, vp, vp, sz, vp]),
             "oversketch_device_status": (st, [vp, ctypes.POINTER(i32), i32]),
             "oversketch_sketch_left_noalloc": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, u64, vp]),
+            "oversketch_gemm_bf16": (st, [vp, i64, vp, i64, i64, i64, i64, f32, f32, vp, i64, vp]),
+            "oversketch_select_transpose": (st, [vp, st, i64, i64, i64, u64, i32, vp, st, i64, vp]),
+            "oversketch_cast": (st, [vp, st, i64, i64, i64, vp, st, i64, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -93,7 +96,8 @@ def _sigs_names():
             "oversketch_plan_destroy", "oversketch_sketch_workspace", "oversketch_sketch_left",
             "oversketch_sketch_right", "oversketch_gemm_masked", "oversketch_workspace_size",
             "oversketch_matmul", "oversketch_unsketch_cols", "oversketch_unsketch_rows",
-            "oversketch_frob", "oversketch_device_status", "oversketch_sketch_left_noalloc"]
+            "oversketch_frob", "oversketch_device_status", "oversketch_sketch_left_noalloc",
+            "oversketch_gemm_bf16", "oversketch_select_transpose", "oversketch_cast"]
 
 
 def _check(status: int, what: str):
@@ -363,4 +367,41 @@ def sketch_left_noalloc(p: Plan, A: torch.Tensor, out: torch.Tensor, out_dtype="
     _check(load_library().oversketch_sketch_left_noalloc(
         p.handle, _ptr(A), _dt(A), A.shape[0], lda, _ptr(out), od, out.stride(0), _ptr(scales),
         _ptr(col_scale), block_mask, _stream(stream)), "oversketch_sketch_left_noalloc")
+    return out
+
+
+def gemm_bf16(A, B, alpha=1.0, beta=0.0, C=None, stream=None):
+    """C = alpha * A . B^T (+ beta C) on the tensor cores; A m x K, B n x K, BF16 K-major."""
+    lda, ldb = _rowmajor(A, "A"), _rowmajor(B, "B")
+    m, K = A.shape
+    n = B.shape[0]
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float32, device=A.device)
+    _check(load_library().oversketch_gemm_bf16(_ptr(A), lda, _ptr(B), ldb, m, n, K, alpha, beta, _ptr(C),
+                                               C.stride(0), _stream(stream)), "oversketch_gemm_bf16")
+    return C
+
+
+def select_transpose(X, out_dtype=None, block_mask=0, b=0, out=None, stream=None):
+    """Y = X[:, selected columns]^T with an optional dtype conversion."""
+    ldx = _rowmajor(X, "X")
+    rows, cols = X.shape
+    od = _dtype_code(out_dtype) if out_dtype is not None else _dt(X)
+    ocols = cols if not block_mask else bin(block_mask).count("1") * b
+    if out is None:
+        out = torch.empty((ocols, _pad_ld(rows, od)), dtype=_TORCH_DT[od], device=X.device)[:, :rows]
+    _check(load_library().oversketch_select_transpose(_ptr(X), _dt(X), rows, cols, ldx, block_mask, b, _ptr(out),
+                                                      od, out.stride(0), _stream(stream)),
+           "oversketch_select_transpose")
+    return out
+
+
+def cast(X, out_dtype, out=None, stream=None):
+    ldx = _rowmajor(X, "X")
+    rows, cols = X.shape
+    od = _dtype_code(out_dtype)
+    if out is None:
+        out = torch.empty((rows, _pad_ld(cols, od)), dtype=_TORCH_DT[od], device=X.device)[:, :cols]
+    _check(load_library().oversketch_cast(_ptr(X), _dt(X), rows, cols, ldx, _ptr(out), od, out.stride(0),
+                                          _stream(stream)), "oversketch_cast")
     return out

@@ -185,10 +185,18 @@ def test_unsketch_parity(ops):
     z = (N + e) * b
     T = rng.standard_normal((m, z)).astype(np.float32)
     U = rng.standard_normal((z, l)).astype(np.float32)
+    cols = oracle.selected_columns(mask, N + e, b)
+    # the kernels take the kept blocks only, compacted; the oracle reads them in place
+    T_sel = np.ascontiguousarray(T[:, cols])
+    U_sel = np.ascontiguousarray(U[cols])
+    T[:, np.setdiff1d(np.arange(z), cols)] = np.nan     # dropped blocks must never be read
+    U[np.setdiff1d(np.arange(z), cols)] = np.nan
     p = ops.plan(n, b, N, e, 2)
     h, s = oracle.hash_tables(n, b, N, e, 2)
-    dX = ops.unsketch_cols(p, _dev(T), mask, 0.25).cpu().numpy()
-    dG = ops.unsketch_rows(p, _dev(U), mask, 0.25).cpu().numpy()
+    dX = ops.unsketch_cols(p, _dev(T_sel), mask, 0.25).cpu().numpy()
+    dG = ops.unsketch_rows(p, _dev(U_sel), mask, 0.25).cpu().numpy()
+    T = np.nan_to_num(T)
+    U = np.nan_to_num(U)
     ref_x = oracle.unsketch_cols(T, h, s, b, mask, 0.25)
     ref_g = oracle.unsketch_rows(U, h, s, b, mask, 0.25)
     # 4 kept terms: FP32 bound with 5 roundings (4 adds + the scale)
