@@ -66,7 +66,10 @@ typedef enum {
 typedef enum {
     OS_F32 = 0,               /* IEEE binary32                              */
     OS_BF16 = 1,              /* bfloat16, round-to-nearest-even            */
-    OS_FP8E4M3 = 2            /* OCP FP8 E4M3 + per-(row, 128-q) power-of-2 */
+    OS_FP8E4M3 = 2,           /* OCP FP8 E4M3 + per-(row, 128-q) power-of-2 */
+    OS_TF32X2 = 3             /* FP32 as two planes hi + lo: hi = x with the low 13
+                                 mantissa bits cleared (exact in TF32), lo = x - hi;
+                                 plane lo follows plane hi (rows * ld elements) */
 } os_dtype;
 
 /* Human-readable name of a status code (static storage). */

@@ -63,18 +63,26 @@ struct MatmulLayout {
     size_t at_bytes, bt_bytes, as_bytes, bs_bytes, left_ws;
 };
 
+// dtype of the sketched operands for a GEMM dtype: FP32 products run on the
+// tensor cores as 3xTF32 (operands split into hi/lo planes by the sketch) when
+// the block width fits the 32-element K tile, else on the FFMA kernel.
+os_dtype sketch_dtype(const Plan *p, os_dtype g) {
+    return (g == OS_F32 && p->b % 32 == 0) ? OS_TF32X2 : g;
+}
+
 MatmulLayout layout(const Plan *p, int64_t m, int64_t l, os_dtype a_t, os_dtype b_t, const os_opts *o) {
     MatmulLayout L;
-    const os_dtype g = o ? o->gemm_dtype : OS_F32;
+    const os_dtype g = sketch_dtype(p, o ? o->gemm_dtype : OS_F32);
     const size_t es = dtype_size(g);
+    const size_t planes = g == OS_TF32X2 ? 2 : 1;
     L.z = (int64_t)p->P * p->b;
     const int64_t align_el = 16 / (int64_t)es;
     L.ldat = (L.z + align_el - 1) / align_el * align_el;
     L.ldbt = L.ldat;
     L.nsl = (L.z + 127) / 128;
-    L.at_bytes = align256((size_t)m * L.ldat * es);
+    L.at_bytes = align256((size_t)m * L.ldat * es * planes);
     const bool sym = o && o->symmetric;
-    L.bt_bytes = sym ? 0 : align256((size_t)l * L.ldbt * es);
+    L.bt_bytes = sym ? 0 : align256((size_t)l * L.ldbt * es * planes);
     L.as_bytes = g == OS_FP8E4M3 ? align256((size_t)m * L.nsl * 4) : 0;
     L.bs_bytes = (g == OS_FP8E4M3 && !sym) ? align256((size_t)l * L.nsl * 4) : 0;
     // the packed-strip buffer is reused by the left and then the right sketch
@@ -168,6 +176,7 @@ extern "C" os_status oversketch_gemm_masked(oversketch_plan_t plan, const void *
                                    alpha, beta, C, ldc, st);
         case OS_BF16:
         case OS_FP8E4M3:
+        case OS_TF32X2:
             return gemm_masked_tc(p, At, ldat, a_scales, BtT, ldbt, b_scales, dt, m, l, mask, alpha,
                                   beta, C, ldc, st);
     }
@@ -196,8 +205,9 @@ extern "C" os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os
     if (!sym && !B) return OS_ERR_INVALID_ARG;
     if (n != p->n || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_mask(mask, p->P));
-    const os_dtype g = opts ? opts->gemm_dtype : OS_F32;
-    if (g != OS_F32 && g != OS_BF16 && g != OS_FP8E4M3) return OS_ERR_DTYPE;
+    const os_dtype g0 = opts ? opts->gemm_dtype : OS_F32;
+    if (g0 != OS_F32 && g0 != OS_BF16 && g0 != OS_FP8E4M3 && g0 != OS_TF32X2) return OS_ERR_DTYPE;
+    const os_dtype g = sketch_dtype(p, g0);
     const MatmulLayout L = layout(p, m, l, a_t, b_t, opts);
     const size_t need = L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes + L.left_ws + 256;
     if (!workspace || ws_bytes < need) return OS_ERR_WORKSPACE;

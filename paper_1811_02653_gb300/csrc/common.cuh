@@ -49,9 +49,14 @@ os_status check_mask(uint64_t mask, int P);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-inline size_t dtype_size(os_dtype t) {
-    return t == OS_F32 ? 4 : (t == OS_BF16 ? 2 : 1);
+inline size_t dtype_size(os_dtype t) {   // bytes per element of one plane
+    return (t == OS_F32 || t == OS_TF32X2) ? 4 : (t == OS_BF16 ? 2 : 1);
 }
+
+// Output tag of the sketch kernels for OS_TF32X2 (two FP32 planes hi, lo).
+struct Tf32Pair {
+    float v;
+};
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 

@@ -33,20 +33,41 @@ namespace {
 
 using namespace tc;
 
-constexpr int BM = 128, BN = 256, BK = 64;
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;          // 16 KB
-constexpr int B_BYTES = BN * BK * 2;          // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TMEM_COLS = 512;                // 2 accumulators of 256 columns
+constexpr int BM = 128;
+constexpr int ROWB = 128;                     // bytes per tile row: one 128-byte swizzle row
 constexpr int kThreads = 192;
-constexpr size_t kSmemBytes = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+
+// Tile configuration.  kPlanes = 1: BF16 operands (64 K-elements per stage row,
+// tcgen05 kind::f16).  kPlanes = 2: FP32 operands given as two TF32-exact
+// planes hi/lo (32 K-elements per stage row, kind::tf32, three products
+// hi.hi + hi.lo + lo.hi per K step: FP32-level accuracy on the tensor cores).
+template <int kBN, int kStages, int kPlanes>
+struct Cfg {
+    static constexpr int BN = kBN;
+    static constexpr int STAGES = kStages;
+    static constexpr int PLANES = kPlanes;
+    static constexpr int ELEM = kPlanes == 1 ? 2 : 4;         // bytes per element
+    static constexpr int BKE = ROWB / ELEM;                    // K elements per stage
+    static constexpr int A_BYTES = BM * ROWB;                  // one plane of A
+    static constexpr int B_BYTES = BN * ROWB;                  // one plane of B
+    static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
+    static constexpr int TMEM_COLS = 2 * BN;                   // two accumulators
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+    static constexpr uint32_t IDESC = kPlanes == 1 ? idesc_bf16_f32(BM, BN) : idesc_tf32_f32(BM, BN);
+    // 3xTF32: the tensor core accumulates each chunk of CHUNK_KB K blocks (K = 256)
+    // in TMEM and the epilogue adds the chunks in FP32 registers, so the
+    // accumulation error does not grow with K.  BF16: one chunk per tile.
+    static constexpr int CHUNK_KB = kPlanes == 2 ? 8 : (1 << 30);
+};
+
+using CfgBf16 = Cfg<256, 4, 1>;
+using CfgTf32x3 = Cfg<128, 3, 2>;
 
 struct GemmArgs {
     int64_t m, l;
-    int32_t b;            // block width (multiple of 64)
-    int32_t kb_per_blk;   // b / 64
-    int32_t num_kb;       // k * b / 64
+    int32_t b;            // block width (multiple of the stage's K elements)
+    int32_t kb_per_blk;   // b / BKE
+    int32_t num_kb;       // k * b / BKE
     int32_t tiles_m, tiles_n, num_tiles;
     float alpha, beta;
     float *C;
@@ -65,14 +86,18 @@ __device__ __forceinline__ void tile_coords(const GemmArgs &g, int t, int &tm, i
     tn = in / gm;
 }
 
+// tmap_a0/b0: BF16 operands or the TF32 hi planes; tmap_a1/b1: the lo planes.
+template <class C>
 __global__ void __launch_bounds__(kThreads, 1)
-gemm_masked_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
-                        const __grid_constant__ CUtensorMap tmap_b, const GemmArgs g) {
+gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_constant__ CUtensorMap tmap_b0,
+                      const __grid_constant__ CUtensorMap tmap_a1, const __grid_constant__ CUtensorMap tmap_b1,
+                      const GemmArgs g) {
+    constexpr int STAGES = C::STAGES, BN = C::BN, BKE = C::BKE;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *tiles = smem;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint8_t *tiles = smem;   // stage s: [A plane 0][A plane 1][B plane 0][B plane 1]
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_BYTES);
     uint64_t *empty = full + STAGES;
     uint64_t *tmem_full = empty + STAGES;
     uint64_t *tmem_empty = tmem_full + 2;
@@ -94,10 +119,14 @@ gemm_masked_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
         mbar_init(drain, 1);
         *abort = 0;
         fence_barrier_init();
-        prefetch_tmap(&tmap_a);
-        prefetch_tmap(&tmap_b);
+        prefetch_tmap(&tmap_a0);
+        prefetch_tmap(&tmap_b0);
+        if (C::PLANES == 2) {
+            prefetch_tmap(&tmap_a1);
+            prefetch_tmap(&tmap_b1);
+        }
     }
-    if (warp == 1) tmem_alloc(tmem_base_slot, TMEM_COLS);
+    if (warp == 1) tmem_alloc(tmem_base_slot, C::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -118,12 +147,14 @@ gemm_masked_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                 for (int kb = 0; kb < g.num_kb; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
                     const int blk = kb / g.kb_per_blk;
-                    const int kz = g.kept.idx[blk] * g.b + (kb - blk * g.kb_per_blk) * BK;
-                    uint8_t *sa = tiles + stage * STAGE_BYTES;
-                    uint8_t *sb = sa + A_BYTES;
-                    mbar_expect_tx(&full[stage], STAGE_BYTES);
-                    tma_load_2d(&tmap_a, &full[stage], sa, kz, tm * BM);
-                    tma_load_2d(&tmap_b, &full[stage], sb, kz, tn * BN);
+                    const int kz = g.kept.idx[blk] * g.b + (kb - blk * g.kb_per_blk) * BKE;
+                    uint8_t *st = tiles + stage * C::STAGE_BYTES;
+                    mbar_expect_tx(&full[stage], C::STAGE_BYTES);
+                    tma_load_2d(&tmap_a0, &full[stage], st, kz, tm * BM);
+                    if (C::PLANES == 2) tma_load_2d(&tmap_a1, &full[stage], st + C::A_BYTES, kz, tm * BM);
+                    uint8_t *sb = st + C::PLANES * C::A_BYTES;
+                    tma_load_2d(&tmap_b0, &full[stage], sb, kz, tn * BN);
+                    if (C::PLANES == 2) tma_load_2d(&tmap_b1, &full[stage], sb + C::B_BYTES, kz, tn * BN);
                     issued[stage] = true;
                     issued_phase[stage] = phase;
                     if (++stage == STAGES) stage = 0, phase ^= 1u;
@@ -136,28 +167,38 @@ gemm_masked_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
             int stage = 0;
             uint32_t phase = 0;
             int iter = 0;
             bool ok = true;
             bool any = false;
-            for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x, ++iter) {
+            for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
+              for (int kc = 0; ok && kc < g.num_kb; kc += C::CHUNK_KB, ++iter) {
+                const int kc_end = min(g.num_kb, kc + C::CHUNK_KB);
                 const int a = iter & 1;
                 const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
                 if (!mbar_wait(&tmem_empty[a], aphase ^ 1u, abort)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(a * BN);
-                for (int kb = 0; kb < g.num_kb; ++kb) {
+                for (int kb = kc; kb < kc_end; ++kb) {
                     if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(tiles + stage * STAGE_BYTES);
-                    const uint32_t sb = sa + A_BYTES;
+                    const uint32_t sa0 = smem_u32(tiles + stage * C::STAGE_BYTES);
+                    const uint32_t sb0 = sa0 + C::PLANES * C::A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t ad = sdesc_kmajor_sw128(sa + kk * 32);
-                        const uint64_t bd = sdesc_kmajor_sw128(sb + kk * 32);
-                        umma_f16(d, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < ROWB / 32; ++kk) {
+                        const uint32_t acc0 = (kb > kc || kk > 0) ? 1u : 0u;
+                        const uint64_t ad = sdesc_kmajor_sw128(sa0 + kk * 32);
+                        const uint64_t bd = sdesc_kmajor_sw128(sb0 + kk * 32);
+                        if constexpr (C::PLANES == 1) {
+                            umma_f16(d, ad, bd, C::IDESC, acc0);
+                        } else {
+                            const uint64_t adl = sdesc_kmajor_sw128(sa0 + C::A_BYTES + kk * 32);
+                            const uint64_t bdl = sdesc_kmajor_sw128(sb0 + C::B_BYTES + kk * 32);
+                            umma_tf32(d, ad, bd, C::IDESC, acc0);     // hi . hi
+                            umma_tf32(d, ad, bdl, C::IDESC, 1u);      // hi . lo
+                            umma_tf32(d, adl, bd, C::IDESC, 1u);      // lo . hi
+                        }
                     }
                     any = true;
                     umma_commit(&empty[stage]);
@@ -165,6 +206,7 @@ gemm_masked_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
                 }
                 if (!ok) break;
                 umma_commit(&tmem_full[a]);
+              }
             }
             if (!ok && any) {
                 // Drain: wait for the MMAs already issued before freeing TMEM.
@@ -178,53 +220,79 @@ gemm_masked_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
         const int row_in_tile = quarter * 32 + lane;
         int iter = 0;
         const bool vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15u) == 0) && (g.ldc % 4 == 0);
-        for (int t = blockIdx.x; t < g.num_tiles; t += gridDim.x, ++iter) {
-            const int a = iter & 1;
-            const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
-            // warp-uniform decision: tcgen05.ld below is a .sync.aligned instruction
-            if (!__all_sync(0xffffffffu, mbar_wait(&tmem_full[a], aphase, abort))) break;
-            tc_fence_after();
+        // FP32 store of 32 consecutive values of row r starting at column cbase
+        auto store32 = [&](int64_t r, int64_t cbase, const float *val) {
+            if (r >= g.m) return;
+            float *dst = g.C + r * g.ldc + cbase;
+            if (vec_ok && cbase + 32 <= g.l) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    float4 o = make_float4(g.alpha * val[4 * u + 0], g.alpha * val[4 * u + 1],
+                                           g.alpha * val[4 * u + 2], g.alpha * val[4 * u + 3]);
+                    if (g.beta != 0.f) {
+                        const float4 old = *reinterpret_cast<const float4 *>(dst + 4 * u);
+                        o.x = fmaf(g.beta, old.x, o.x);
+                        o.y = fmaf(g.beta, old.y, o.y);
+                        o.z = fmaf(g.beta, old.z, o.z);
+                        o.w = fmaf(g.beta, old.w, o.w);
+                    }
+                    *reinterpret_cast<float4 *>(dst + 4 * u) = o;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                    if (cbase + u < g.l) {
+                        float o = g.alpha * val[u];
+                        if (g.beta != 0.f) o = fmaf(g.beta, dst[u], o);
+                        dst[u] = o;
+                    }
+                }
+            }
+        };
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
             int tm, tn;
             tile_coords(g, t, tm, tn);
             const int64_t r = (int64_t)tm * BM + row_in_tile;
             const int64_t c0 = (int64_t)tn * BN;
-            for (int ch = 0; ch < BN / 32; ++ch) {
-                uint32_t v[32];
-                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN + ch * 32), v);
-                if (r < g.m) {
-                    float *dst = g.C + r * g.ldc + c0 + ch * 32;
-                    const int64_t cbase = c0 + ch * 32;
-                    if (vec_ok && cbase + 32 <= g.l) {
+            if constexpr (C::CHUNK_KB < (1 << 30)) {
+                // chunked accumulation: running FP32 sum of the tile row in registers
+                float total[BN];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            float4 o;
-                            o.x = g.alpha * __uint_as_float(v[4 * u + 0]);
-                            o.y = g.alpha * __uint_as_float(v[4 * u + 1]);
-                            o.z = g.alpha * __uint_as_float(v[4 * u + 2]);
-                            o.w = g.alpha * __uint_as_float(v[4 * u + 3]);
-                            if (g.beta != 0.f) {
-                                const float4 old = *reinterpret_cast<const float4 *>(dst + 4 * u);
-                                o.x = fmaf(g.beta, old.x, o.x);
-                                o.y = fmaf(g.beta, old.y, o.y);
-                                o.z = fmaf(g.beta, old.z, o.z);
-                                o.w = fmaf(g.beta, old.w, o.w);
-                            }
-                            *reinterpret_cast<float4 *>(dst + 4 * u) = o;
-                        }
-                    } else {
+                for (int u = 0; u < BN; ++u) total[u] = 0.f;
+                for (int kc = 0; kc < g.num_kb; kc += C::CHUNK_KB, ++iter) {
+                    const int a = iter & 1;
+                    const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+                    // warp-uniform decision: tcgen05.ld below is a .sync.aligned instruction
+                    if (!__all_sync(0xffffffffu, mbar_wait(&tmem_full[a], aphase, abort))) { ok = false; break; }
+                    tc_fence_after();
 #pragma unroll
-                        for (int u = 0; u < 32; ++u) {
-                            if (cbase + u < g.l) {
-                                float o = g.alpha * __uint_as_float(v[u]);
-                                if (g.beta != 0.f) o = fmaf(g.beta, dst[u], o);
-                                dst[u] = o;
-                            }
-                        }
+                    for (int ch = 0; ch < BN / 32; ++ch) {
+                        uint32_t v[32];
+                        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN + ch * 32), v);
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) total[ch * 32 + u] += __uint_as_float(v[u]);
                     }
+                    tc_fence_before();
+                    mbar_arrive(&tmem_empty[a]);
                 }
+                if (!ok) break;
+#pragma unroll
+                for (int ch = 0; ch < BN / 32; ++ch) store32(r, c0 + ch * 32, total + ch * 32);
+            } else {
+                const int a = iter & 1;
+                const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+                ++iter;
+                if (!__all_sync(0xffffffffu, mbar_wait(&tmem_full[a], aphase, abort))) break;
+                tc_fence_after();
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t v[32];
+                    tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN + ch * 32), v);
+                    store32(r, c0 + ch * 32, reinterpret_cast<const float *>(v));
+                }
+                tc_fence_before();
+                mbar_arrive(&tmem_empty[a]);
             }
-            tc_fence_before();
-            mbar_arrive(&tmem_empty[a]);
         }
     }
 
@@ -233,7 +301,7 @@ gemm_masked_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a,
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem_base, TMEM_COLS);
+        tmem_dealloc(tmem_base, C::TMEM_COLS);
     }
 }
 
@@ -288,40 +356,58 @@ int num_sms() {
 
 namespace {
 
-// C = alpha * sum over the listed K blocks of A_blk . B_blk^T (+ beta C); A rows x zK
-// and B cols x zK are K-major BF16 with zK columns in total.
-os_status launch_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l,
-                      int64_t zK, int32_t blk, const BlockList &kept, float alpha, float beta, float *C,
-                      int64_t ldc, cudaStream_t st) {
-    if (blk % BK != 0) return OS_ERR_UNSUPPORTED;
-    if (!aligned16(A) || !aligned16(B) || (lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0) return OS_ERR_INVALID_ARG;
+// C = alpha * sum over the listed K blocks of A_blk . B_blk^T (+ beta C).  A is
+// rows x zK, B cols x zK, K-major; for the TF32 configuration A1/B1 are the lo
+// planes (A0/B0 the hi planes).
+template <class C>
+os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0, const void *B1, int64_t ldb,
+                    int64_t m, int64_t l, int64_t zK, int32_t blk, const BlockList &kept, float alpha, float beta,
+                    float *Cout, int64_t ldc, cudaStream_t st) {
+    if (blk % C::BKE != 0) return OS_ERR_UNSUPPORTED;
+    if (!aligned16(A0) || !aligned16(B0) || (lda * C::ELEM) % 16 != 0 || (ldb * C::ELEM) % 16 != 0)
+        return OS_ERR_INVALID_ARG;
+    if (C::PLANES == 2 && (!aligned16(A1) || !aligned16(B1))) return OS_ERR_INVALID_ARG;
     if (zK >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
     GemmArgs g;
     g.m = m;
     g.l = l;
     g.b = blk;
-    g.kb_per_blk = blk / BK;
+    g.kb_per_blk = blk / C::BKE;
     g.kept = kept;
     g.num_kb = kept.count * g.kb_per_blk;
     g.tiles_m = (int)((m + BM - 1) / BM);
-    g.tiles_n = (int)((l + BN - 1) / BN);
+    g.tiles_n = (int)((l + C::BN - 1) / C::BN);
     g.num_tiles = g.tiles_m * g.tiles_n;
     g.alpha = alpha;
     g.beta = beta;
-    g.C = C;
+    g.C = Cout;
     g.ldc = ldc;
-    CUtensorMap ta, tb;
-    OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, zK, lda, BM, BK));
-    OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, zK, ldb, BN, BK));
+    const CUtensorMapDataType dt = C::PLANES == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUtensorMap ta0, tb0, ta1, tb1;
+    OSK_TRY(make_tmap(&ta0, A0, dt, C::ELEM, m, zK, lda, BM, C::BKE));
+    OSK_TRY(make_tmap(&tb0, B0, dt, C::ELEM, l, zK, ldb, C::BN, C::BKE));
+    if (C::PLANES == 2) {
+        OSK_TRY(make_tmap(&ta1, A1, dt, C::ELEM, m, zK, lda, BM, C::BKE));
+        OSK_TRY(make_tmap(&tb1, B1, dt, C::ELEM, l, zK, ldb, C::BN, C::BKE));
+    } else {
+        ta1 = ta0;
+        tb1 = tb0;
+    }
     static bool attr_set = false;
     if (!attr_set) {
-        OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_masked_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kSmemBytes));
+        OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_masked_tc_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)C::SMEM));
         attr_set = true;
     }
     const int grid = g.num_tiles < num_sms() ? g.num_tiles : num_sms();
-    gemm_masked_bf16_kernel<<<grid, kThreads, kSmemBytes, st>>>(ta, tb, g);
+    gemm_masked_tc_kernel<C><<<grid, kThreads, C::SMEM, st>>>(ta0, tb0, ta1, tb1, g);
     return check_launch();
+}
+
+os_status launch_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l, int64_t zK,
+                      int32_t blk, const BlockList &kept, float alpha, float beta, float *C, int64_t ldc,
+                      cudaStream_t st) {
+    return launch_tc<CfgBf16>(A, nullptr, lda, B, nullptr, ldb, m, l, zK, blk, kept, alpha, beta, C, ldc, st);
 }
 
 }  // namespace
@@ -332,9 +418,16 @@ os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const floa
                          cudaStream_t st) {
     (void)a_scales;
     (void)b_scales;
-    if (dt != OS_BF16) return OS_ERR_UNSUPPORTED;
-    return launch_bf16(At, ldat, BtT, ldbt, m, l, (int64_t)p->P * p->b, p->b, mask_to_list(mask, p->P), alpha,
-                       beta, C, ldc, st);
+    const int64_t z = (int64_t)p->P * p->b;
+    const BlockList kept = mask_to_list(mask, p->P);
+    if (dt == OS_BF16) return launch_bf16(At, ldat, BtT, ldbt, m, l, z, p->b, kept, alpha, beta, C, ldc, st);
+    if (dt == OS_TF32X2) {
+        // two planes per operand: hi at the pointer, lo one plane (rows * ld elements) later
+        const float *a0 = (const float *)At, *b0 = (const float *)BtT;
+        return launch_tc<CfgTf32x3>(a0, a0 + m * ldat, ldat, b0, b0 + l * ldbt, ldbt, m, l, z, p->b, kept, alpha,
+                                    beta, C, ldc, st);
+    }
+    return OS_ERR_UNSUPPORTED;
 }
 
 }  // namespace osk

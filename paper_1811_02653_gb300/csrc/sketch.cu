@@ -101,7 +101,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                      const uint32_t *__restrict__ pperm, const uint32_t *__restrict__ poffs,
                      int64_t pstride, int32_t b, int32_t z, const float *__restrict__ col_scale,
                      OutT *__restrict__ Yt, int64_t ldy, float *__restrict__ scales,
-                     int64_t lds, BlockList blocks, int32_t tiles_per_block) {
+                     int64_t lds, BlockList blocks, int32_t tiles_per_block, int64_t plane_elems) {
     constexpr int SUBS = 32 / SLOTS;     // lanes per member
     constexpr int TF = 4 * SUBS;         // free indices per CTA (one strip)
     constexpr int PITCH = TF + 1;        // odd pitch: conflict-free column reads
@@ -229,6 +229,18 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                 }
             }
             if (lane == 0) scales[frow * lds + q0 / 128] = ldexpf(1.f, e);
+        } else if constexpr (std::is_same<OutT, Tf32Pair>::value) {
+            // FP32 as hi + lo: hi keeps 10 mantissa bits (exact in TF32), lo = x - hi (exact)
+            float *d0 = reinterpret_cast<float *>(dst);
+#pragma unroll
+            for (int k = 0; k < VPL; ++k) {
+                const int q = q0 + lane + 32 * k;
+                if (q < qend) {
+                    const float hi = __uint_as_float(__float_as_uint(v[k]) & 0xffffe000u);
+                    d0[lane + 32 * k] = hi;
+                    d0[plane_elems + lane + 32 * k] = v[k] - hi;
+                }
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < VPL; ++k) {
@@ -372,7 +384,7 @@ __global__ void __launch_bounds__(256) unsketch_rows_kernel(
 template <typename InT, typename OutT, int QT, int SLOTS>
 os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int64_t ldx, int64_t F,
                           const float *col_scale, void *Yt, int64_t ldy, float *scales,
-                          const BlockList &blocks, cudaStream_t st) {
+                          const BlockList &blocks, cudaStream_t st, int64_t plane_elems = 0) {
     const int z = p->P * p->b;
     const int tpb = (p->b + QT - 1) / QT;
     constexpr int TF = 128 / SLOTS;
@@ -383,12 +395,12 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
         auto k = sketch_gather_kernel<InT, OutT, QT, true, SLOTS>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
-                                          col_scale, (OutT *)Yt, ldy, scales, z / 128, blocks, tpb);
+                                          col_scale, (OutT *)Yt, ldy, scales, z / 128, blocks, tpb, plane_elems);
     } else {
         auto k = sketch_gather_kernel<InT, OutT, QT, false, SLOTS>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
-                                          nullptr, (OutT *)Yt, ldy, scales, z / 128, blocks, tpb);
+                                          nullptr, (OutT *)Yt, ldy, scales, z / 128, blocks, tpb, plane_elems);
     }
     return check_launch();
 }
@@ -398,7 +410,8 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
 // keep the CTAs that run together on few strips.
 template <typename InT>
 os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *col_scale, void *Yt,
-                        os_dtype out_t, int64_t ldy, float *scales, uint64_t block_mask, cudaStream_t st) {
+                        os_dtype out_t, int64_t ldy, float *scales, uint64_t block_mask, cudaStream_t st,
+                        int64_t plane_rows = 0) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
     const int64_t ss = p->n * kStrip;
     switch (out_t) {
@@ -410,6 +423,9 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *co
         case OS_FP8E4M3:
             return launch_gather_t<InT, __nv_fp8_e4m3, 128, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales,
                                                                blocks, st);
+        case OS_TF32X2:
+            return launch_gather_t<InT, Tf32Pair, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, blocks,
+                                                         st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
 }
@@ -418,7 +434,8 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *co
 // pieces: one address translation per 512 bytes is cheap enough that no
 // packing pass is needed).  F must be a multiple of 128.
 os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, void *Yt, os_dtype out_t,
-                               int64_t ldy, float *scales, uint64_t block_mask, cudaStream_t st) {
+                               int64_t ldy, float *scales, uint64_t block_mask, cudaStream_t st,
+                               int64_t plane_rows = 0) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
     switch (out_t) {
         case OS_F32:
@@ -429,6 +446,9 @@ os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64
         case OS_FP8E4M3:
             return launch_gather_t<float, __nv_fp8_e4m3, 128, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, scales,
                                                                  blocks, st);
+        case OS_TF32X2:
+            return launch_gather_t<float, Tf32Pair, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, blocks,
+                                                           st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
 }
@@ -462,7 +482,7 @@ os_status check_out(const Plan *p, int64_t rows, void *Yt, os_dtype out_t, int64
                     float *scales) {
     const int64_t z = (int64_t)p->P * p->b;
     if (!Yt || rows < 0) return OS_ERR_INVALID_ARG;
-    if (out_t != OS_F32 && out_t != OS_BF16 && out_t != OS_FP8E4M3) return OS_ERR_DTYPE;
+    if (out_t != OS_F32 && out_t != OS_BF16 && out_t != OS_FP8E4M3 && out_t != OS_TF32X2) return OS_ERR_DTYPE;
     if (ldy < z) return OS_ERR_INVALID_ARG;
     if (!aligned16(Yt) || (ldy * (int64_t)dtype_size(out_t)) % 16 != 0) return OS_ERR_INVALID_ARG;
     if (out_t == OS_FP8E4M3) {
@@ -499,11 +519,12 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
     void *Xs = ws_base(ws);
     if (a_t == OS_F32) {
         OSK_TRY(launch_pack_cols<float>((const float *)A, lda, m, p->n, (float *)Xs, st));
-        return launch_gather<float>(p, (const float *)Xs, m, col_scale, At, out_t, ldat, scales, block_mask, st);
+        return launch_gather<float>(p, (const float *)Xs, m, col_scale, At, out_t, ldat, scales, block_mask, st,
+                                    m);
     }
     OSK_TRY(launch_pack_cols<__nv_bfloat16>((const __nv_bfloat16 *)A, lda, m, p->n, (__nv_bfloat16 *)Xs, st));
     return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, m, col_scale, At, out_t, ldat, scales,
-                                        block_mask, st);
+                                        block_mask, st, m);
 }
 
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
@@ -521,24 +542,24 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
                         l >= kStrip;
     if (direct) {
         const int64_t lf = l / kStrip * kStrip;
-        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, BtT, out_t, ldbt, scales, block_mask, st));
+        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, BtT, out_t, ldbt, scales, block_mask, st, l));
         if (lf == l) return OS_OK;
         if (!ws || ws_bytes < sketch_workspace_bytes(p, l - lf, b_t)) return OS_ERR_WORKSPACE;
         float *Xs = (float *)ws_base(ws);
         OSK_TRY(launch_pack_rows<float>((const float *)B + lf, ldb, p->n, l - lf, Xs, st));
         char *yt = (char *)BtT + (size_t)lf * ldbt * dtype_size(out_t);
         float *sc = scales ? scales + lf * ((int64_t)p->P * p->b / 128) : nullptr;
-        return launch_gather<float>(p, Xs, l - lf, nullptr, yt, out_t, ldbt, sc, block_mask, st);
+        return launch_gather<float>(p, Xs, l - lf, nullptr, yt, out_t, ldbt, sc, block_mask, st, l);
     }
     if (!ws || ws_bytes < sketch_workspace_bytes(p, l, b_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);
     if (b_t == OS_F32) {
         OSK_TRY(launch_pack_rows<float>((const float *)B, ldb, p->n, l, (float *)Xs, st));
-        return launch_gather<float>(p, (const float *)Xs, l, nullptr, BtT, out_t, ldbt, scales, block_mask, st);
+        return launch_gather<float>(p, (const float *)Xs, l, nullptr, BtT, out_t, ldbt, scales, block_mask, st, l);
     }
     OSK_TRY(launch_pack_rows<__nv_bfloat16>((const __nv_bfloat16 *)B, ldb, p->n, l, (__nv_bfloat16 *)Xs, st));
     return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, l, nullptr, BtT, out_t, ldbt, scales,
-                                        block_mask, st);
+                                        block_mask, st, l);
 }
 
 os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t ldt, uint64_t mask,

@@ -19,12 +19,13 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liboversketch.so")
 
-F32, BF16, FP8 = 0, 1, 2
+F32, BF16, FP8, TF32X2 = 0, 1, 2, 3
 _DT = {torch.float32: F32, torch.bfloat16: BF16}
 if hasattr(torch, "float8_e4m3fn"):
     _DT[torch.float8_e4m3fn] = FP8
-_TORCH_DT = {F32: torch.float32, BF16: torch.bfloat16, FP8: getattr(torch, "float8_e4m3fn", None)}
-DTYPE_NAMES = {"f32": F32, "fp32": F32, "bf16": BF16, "fp8": FP8, "fp8e4m3": FP8}
+_TORCH_DT = {F32: torch.float32, BF16: torch.bfloat16, FP8: getattr(torch, "float8_e4m3fn", None),
+             TF32X2: torch.float32}
+DTYPE_NAMES = {"f32": F32, "fp32": F32, "bf16": BF16, "fp8": FP8, "fp8e4m3": FP8, "tf32x2": TF32X2}
 FROB_WORKSPACE_BYTES = 12288
 
 _lib = None
@@ -220,6 +221,20 @@ def sketch_workspace(p: Plan, free_extent: int, in_dtype=torch.float32) -> int:
     return out.value
 
 
+def _alloc_out(rows, ld, z, od, device):
+    """Sketch output: rows x z view (row pitch ld); for TF32X2 the hi plane of a
+    (2, rows, ld) buffer whose lo plane follows it."""
+    if od == TF32X2:
+        return torch.empty((2, rows, ld), dtype=torch.float32, device=device)[0, :, :z]
+    return torch.empty((rows, ld), dtype=_TORCH_DT[od], device=device)[:, :z]
+
+
+def tf32_planes(t):
+    """(hi, lo) views of a TF32X2 sketch output."""
+    base = t.as_strided((2, t.shape[0], t.shape[1]), (t.shape[0] * t.stride(0), t.stride(0), 1))
+    return base[0], base[1]
+
+
 def _workspace(p, F, dtype, device, workspace):
     if workspace is None:
         workspace = torch.empty(sketch_workspace(p, F, dtype), dtype=torch.uint8, device=device)
@@ -234,7 +249,7 @@ def sketch_left(p: Plan, A: torch.Tensor, out_dtype="f32", col_scale=None, out=N
     od = _dtype_code(out_dtype)
     ld = _pad_ld(p.z, od)
     if out is None:
-        out = torch.empty((m, ld), dtype=_TORCH_DT[od], device=A.device)[:, :p.z]
+        out = _alloc_out(m, ld, p.z, od, A.device)
     if od == FP8 and scales is None:
         scales = torch.empty(_fp8_scales_shape(m, p.z), dtype=torch.float32, device=A.device)
     workspace = _workspace(p, m, A.dtype, A.device, workspace)
@@ -253,7 +268,7 @@ def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=Non
     od = _dtype_code(out_dtype)
     ld = _pad_ld(p.z, od)
     if out is None:
-        out = torch.empty((l, ld), dtype=_TORCH_DT[od], device=B.device)[:, :p.z]
+        out = _alloc_out(l, ld, p.z, od, B.device)
     if od == FP8 and scales is None:
         scales = torch.empty(_fp8_scales_shape(l, p.z), dtype=torch.float32, device=B.device)
     workspace = _workspace(p, l, B.dtype, B.device, workspace)
@@ -264,8 +279,9 @@ def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=Non
 
 
 def gemm_masked(p: Plan, At, BtT, mask: int, alpha=None, beta=0.0, C=None, a_scales=None,
-                b_scales=None, stream=None):
-    """C = alpha * sum_{j in mask} At_j BtT_j^T (+ beta C); alpha defaults to 1/k."""
+                b_scales=None, dtype=None, stream=None):
+    """C = alpha * sum_{j in mask} At_j BtT_j^T (+ beta C); alpha defaults to 1/k.
+    ``dtype`` overrides the operand dtype (e.g. "tf32x2" for hi/lo planes)."""
     m, l = At.shape[0], BtT.shape[0]
     if alpha is None:
         alpha = 1.0 / bin(mask).count("1")
@@ -273,7 +289,8 @@ def gemm_masked(p: Plan, At, BtT, mask: int, alpha=None, beta=0.0, C=None, a_sca
         C = torch.empty((m, l), dtype=torch.float32, device=At.device)
     _check(load_library().oversketch_gemm_masked(
         p.handle, _ptr(At), At.stride(0), _ptr(a_scales), _ptr(BtT), BtT.stride(0), _ptr(b_scales),
-        _dt(At), m, l, mask, alpha, beta, _ptr(C), C.stride(0), _stream(stream)), "oversketch_gemm_masked")
+        _dtype_code(dtype) if dtype is not None else _dt(At), m, l, mask, alpha, beta, _ptr(C), C.stride(0),
+        _stream(stream)), "oversketch_gemm_masked")
     return C
 
 

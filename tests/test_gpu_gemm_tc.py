@@ -121,3 +121,53 @@ def test_symmetric_product(ops):
     ref = oracle.masked_product(At_q, At_q.T, b, mask)
     assert oracle.rel_frob(H, ref) <= 1e-4
     assert oracle.rel_frob(H, H.T) <= 1e-6
+
+
+def _split_tf32(x):
+    """hi = x with the low 13 mantissa bits cleared (exact in TF32), lo = x - hi."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    hi = (x.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+    return hi, (x - hi).astype(np.float32)
+
+
+@pytest.mark.parametrize("m,l,b,N,e,mask", [(128, 128, 32, 2, 1, 0b011), (300, 700, 128, 3, 2, 0b10101),
+                                            (1000, 130, 1024, 2, 1, 0b110), (1, 1, 64, 1, 0, 0b1)])
+def test_gemm_tf32x3_parity(ops, m, l, b, N, e, mask):
+    # FP32 operands as hi/lo TF32 planes: three tensor-core products give FP32 accuracy
+    rng = np.random.default_rng(m + 7 * l)
+    z = (N + e) * b
+    A = rng.standard_normal((m, z)).astype(np.float32)
+    B = rng.standard_normal((l, z)).astype(np.float32)
+    Ah, Al = _split_tf32(A)
+    Bh, Bl = _split_tf32(B)
+    Abuf = torch.from_numpy(np.stack([Ah, Al])).cuda()
+    Bbuf = torch.from_numpy(np.stack([Bh, Bl])).cuda()
+    p = ops.plan(max(z, 64), b, N, e, 0)
+    C = ops.gemm_masked(p, Abuf[0], Bbuf[0], mask, dtype="tf32x2").cpu().numpy()
+    ref = oracle.masked_product(A.astype(np.float64), B.astype(np.float64).T, b, mask)
+    assert oracle.rel_frob(C, ref) <= 1e-5
+
+
+def test_sketch_tf32x2_planes(ops):
+    m, n, l, b, N, e = 200, 3000, 300, 128, 3, 1
+    rng = np.random.default_rng(17)
+    A = torch.from_numpy(rng.standard_normal((m, n)).astype(np.float32)).cuda()
+    B = torch.from_numpy(rng.standard_normal((n, l)).astype(np.float32)).cuda()
+    p = ops.plan(n, b, N, e, 0)
+    for X, fn in ((A, ops.sketch_left), (B, ops.sketch_right)):
+        ref, _ = fn(p, X, "f32")
+        out, _ = fn(p, X, "tf32x2")
+        hi, lo = ops.tf32_planes(out)
+        hi_u = hi.contiguous().view(torch.int32).cpu().numpy()
+        assert (hi_u & 0x1FFF == 0).all()                     # hi is exact in TF32
+        assert torch.equal(hi + lo, ref)                      # hi + lo is the FP32 sum
+
+
+def test_small_workload_fp32_tensor_path(ops):
+    # matmul with FP32 GEMM dtype runs 3xTF32 on the tensor cores (b % 32 == 0)
+    w = W.SMALL
+    A, B = w.left(), w.right()
+    p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
+    C = ops.matmul(p, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), w.mask, "f32")
+    h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+    assert oracle.rel_frob(C.cpu().numpy(), oracle.oversketch(A, B, h, s, w.b, w.mask)) <= 1e-5

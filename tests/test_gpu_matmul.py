@@ -56,7 +56,8 @@ def test_matmul_fp32_parity(ops, m, n, l, b, N, e, mask):
 
 
 def test_injective_plan_is_exact(ops):
-    # b >= n with an injective hash: S_j S_j^T = I and C = AB up to FP32 rounding
+    # b >= n with an injective hash: S_j S_j^T = I and C = AB up to the FP32 path's
+    # rounding (3xTF32 on the tensor cores: within the FP32 gate of 1e-5)
     n, b, N, e = 200, 256, 3, 1
     rng = np.random.default_rng(3)
     A = rng.standard_normal((96, n)).astype(np.float32)
@@ -65,7 +66,7 @@ def test_injective_plan_is_exact(ops):
     s = np.where(rng.random((N + e, n)) < 0.5, -1, 1).astype(np.int8)
     p = ops.plan_from_tables(h, s, b, N, e)
     C = ops.matmul(p, _dev(A), _dev(B), 0b1011, "f32").cpu().numpy()
-    assert oracle.rel_frob(C, A.astype(np.float64) @ B.astype(np.float64)) < 1e-6
+    assert oracle.rel_frob(C, A.astype(np.float64) @ B.astype(np.float64)) < 1e-5
 
 
 def test_gemm_masked_beta_and_alpha(ops):
