@@ -223,9 +223,11 @@ def run_ours(args):
     del Bt_h
     p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
     gd = args.dtype
+    # the FP32 product runs as 3xTF32 on the tensor cores: sketches emit hi/lo planes
+    sd = "tf32x2" if gd == "f32" and w.b % 32 == 0 else gd
     z = p.z
-    At, a_sc = ops.sketch_left(p, A, gd)
-    BtT, b_sc = ops.sketch_right(p, B, gd)
+    At, a_sc = ops.sketch_left(p, A, sd)
+    BtT, b_sc = ops.sketch_right(p, B, sd)
     C = torch.empty((w.m, w.l), dtype=torch.float32, device=dev)
     # one packed-strip workspace, reused by the left and then the right sketch (as oversketch_matmul does)
     ws_pack = torch.empty(max(ops.sketch_workspace(p, w.m), ops.sketch_workspace(p, w.l)),
@@ -234,9 +236,9 @@ def run_ours(args):
 
     # the same three calls oversketch_matmul makes: only kept blocks are sketched
     def step():
-        ops.sketch_left(p, A, gd, out=At, scales=a_sc, workspace=ws_pack, block_mask=w.mask)
-        ops.sketch_right(p, B, gd, out=BtT, scales=b_sc, block_mask=w.mask, workspace=ws_pack)
-        ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc)
+        ops.sketch_left(p, A, sd, out=At, scales=a_sc, workspace=ws_pack, block_mask=w.mask)
+        ops.sketch_right(p, B, sd, out=BtT, scales=b_sc, block_mask=w.mask, workspace=ws_pack)
+        ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc, dtype=sd)
 
     for _ in range(args.warmup):
         step()
@@ -257,11 +259,11 @@ def run_ours(args):
     for s in range(args.steps):
         e = ev[s]
         e[0].record(stream)
-        ops.sketch_left(p, A, gd, out=At, scales=a_sc, workspace=ws_pack, block_mask=w.mask)
+        ops.sketch_left(p, A, sd, out=At, scales=a_sc, workspace=ws_pack, block_mask=w.mask)
         e[1].record(stream)
-        ops.sketch_right(p, B, gd, out=BtT, scales=b_sc, block_mask=w.mask, workspace=ws_pack)
+        ops.sketch_right(p, B, sd, out=BtT, scales=b_sc, block_mask=w.mask, workspace=ws_pack)
         e[2].record(stream)
-        ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc)
+        ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc, dtype=sd)
         e[3].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -330,19 +332,26 @@ def run_ours(args):
             del A16, Bt16
 
     # ---- dominant kernel and its roofline ----
-    es = {"bf16": 2, "f32": 4, "fp8": 1}[gd]
+    es = {"bf16": 2, "f32": 4, "fp8": 1, "tf32x2": 8}[sd]
     n_kept = w.k
     right_bytes = w.n * w.l * 4 + w.l * n_kept * w.b * es
     gemm_flop = 2.0 * w.m * n_kept * w.b * w.l
     phases = {"sketch_left (pack + gather)": t_left, "sketch_right (pack + gather)": t_right,
               "gemm_masked": t_gemm}
     if t_gemm >= t_right:
-        dom = "gemm_masked_bf16_kernel" if gd == "bf16" else "gemm_masked_f32_kernel"
-        if gd == "bf16":
+        ach = gemm_flop / (t_gemm * 1e-3) / 1e12
+        bound, unit = "tensor", "TFLOP/s"
+        if sd == "bf16":
+            dom = "gemm_masked_tc_kernel<Cfg<256,4,1>> (BF16)"
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-            bound, unit, ach = "tensor", "TFLOP/s", gemm_flop / (t_gemm * 1e-3) / 1e12
+        elif sd == "tf32x2":
+            # three TF32 products per K step at half the BF16 rate: the useful FP32 rate peaks
+            # at 1/6 of the BF16 figure (nominal TF32 : BF16 = 1 : 2)
+            dom = "gemm_masked_tc_kernel<Cfg<128,3,2>> (3xTF32)"
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")) / 6.0
         else:
-            peak, bound, unit, ach = None, "alu", "TFLOP/s", gemm_flop / (t_gemm * 1e-3) / 1e12
+            dom = "gemm_masked_f32_kernel (FFMA)"
+            peak, bound = None, "alu"
         per_launch = {"flop": gemm_flop}
     else:
         dom = "sketch_gather_kernel (right sketch)"
@@ -352,7 +361,7 @@ def run_ours(args):
     # DRAM bytes per launch from one ncu capture of this command (profiles/square_launch_list.md);
     # valid for the square workload with the kernels as they were when captured
     traffic = None
-    if dom == "gemm_masked_bf16_kernel" and (w.m, w.n, w.l) == (16384, 65536, 16384):
+    if sd == "bf16" and dom.startswith("gemm_masked_tc") and (w.m, w.n, w.l) == (16384, 65536, 16384):
         traffic = 3755223808 + 1052628480
     roof = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
             "frac": (ach / peak) if peak else None, "traffic": traffic, "kernel": dom,
