@@ -344,6 +344,10 @@ def run_ours(args):
         if sd == "bf16":
             dom = "gemm_masked_tc_kernel<Cfg<256,4,1>> (BF16)"
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        elif sd == "fp8":
+            # block-scaled E4M3: nominal FP8 : BF16 tensor rate = 2 : 1
+            dom = "gemm_masked_tc_kernel<Cfg<224,4,Fp8>> (E4M3, UE8M0 block scales)"
+            peak = 2.0 * peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         elif sd == "tf32x2":
             # three TF32 products per K step at half the BF16 rate: the useful FP32 rate peaks
             # at 1/6 of the BF16 figure (nominal TF32 : BF16 = 1 : 2)
@@ -382,6 +386,10 @@ def run_ours(args):
         Bt_c = oracle.sketch_right(Bc, h, s, w.b)
         if gd == "bf16":
             C_or = oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(Bt_c), w.b, w.mask)
+        elif gd == "fp8":
+            Aq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(At_r))
+            Bq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(Bt_c.T)).T
+            C_or = oracle.masked_product(Aq, Bq, w.b, w.mask)
         else:
             C_or = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
         C_or_exact_sketch = oracle.masked_product(At_r, Bt_c, w.b, w.mask)

@@ -72,6 +72,10 @@ typedef enum {
                                  plane lo follows plane hi (rows * ld elements) */
 } os_dtype;
 
+/* Entries per slice of an FP8 scale array for `rows` rows (rows rounded up to
+ * a multiple of 4, so every slice starts on a 16-byte boundary). */
+#define OS_FP8_SCALE_LD(rows) ((((rows) + 3) / 4) * 4)
+
 /* Human-readable name of a status code (static storage). */
 OS_API const char *oversketch_status_string(os_status s);
 
@@ -127,11 +131,14 @@ OS_API os_status oversketch_plan_destroy(oversketch_plan_t plan);
  *   col_scale: device FP32 array of n scales s_i, or NULL (s_i = 1); used
  *     for A diag(s) S, e.g. the sqrt(D) of the interior-point Hessian.
  *   At: m x z in dtype out_t with leading dim ldat >= z (z = (N+e)*b).
- *   scales: for out_t == OS_FP8E4M3, device FP32 array m x (z/128), entry
- *     [r, t] = 2^e_rt with e_rt the smallest integer such that the FP32 sums
- *     of slice t of row r are all <= 448 * 2^e_rt in magnitude (1.0 for an
- *     all-zero slice); At holds round-to-nearest-even, saturating E4M3 codes
- *     of (sum / 2^e_rt).  NULL otherwise.  FP8 needs b % 128 == 0.
+ *   scales: for out_t == OS_FP8E4M3, device FP32 array of (z/128) slices of
+ *     OS_FP8_SCALE_LD(m) entries each (slice-major, 16-byte aligned): entry
+ *     [t * OS_FP8_SCALE_LD(m) + r] = 2^e_rt with e_rt the smallest integer
+ *     (clamped to [-127, 127]) such that the FP32 sums of slice t (columns
+ *     128t .. 128t+127) of row r are all <= 448 * 2^e_rt in magnitude (1.0
+ *     for an all-zero slice); At holds round-to-nearest-even, saturating E4M3
+ *     codes of (sum / 2^e_rt).  Entries of padding rows are not written.
+ *     NULL otherwise.  FP8 needs b % 128 == 0.
  *   Sums are accumulated in FP32 in ascending order of i inside a bucket;
  *   BF16 output is the round-to-nearest-even of that FP32 sum.
  *   block_mask: bit j set = compute the columns of block j; 0 = all blocks.
@@ -142,7 +149,8 @@ OS_API os_status oversketch_plan_destroy(oversketch_plan_t plan);
  *     per strip, n rows each) before the bucket gather.
  * oversketch_sketch_right:
  *   BtT[c, j*b + q] = sum_{i : h_j(i) = q} sigma_j(i) * B[i, c]
- *   B: n x l (ldb >= l); BtT: l x z (ldbt >= z); scales l x (z/128) for FP8;
+ *   B: n x l (ldb >= l); BtT: l x z (ldbt >= z); FP8 scales as above with
+ *   OS_FP8_SCALE_LD(l) entries per slice;
  *   block_mask as above; workspace of oversketch_sketch_workspace(plan, l, b_t)
  *   bytes.
  * Errors: OS_ERR_INVALID_ARG (null pointers, ld too small, out pointers or

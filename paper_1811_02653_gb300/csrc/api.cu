@@ -83,8 +83,8 @@ MatmulLayout layout(const Plan *p, int64_t m, int64_t l, os_dtype a_t, os_dtype 
     L.at_bytes = align256((size_t)m * L.ldat * es * planes);
     const bool sym = o && o->symmetric;
     L.bt_bytes = sym ? 0 : align256((size_t)l * L.ldbt * es * planes);
-    L.as_bytes = g == OS_FP8E4M3 ? align256((size_t)m * L.nsl * 4) : 0;
-    L.bs_bytes = (g == OS_FP8E4M3 && !sym) ? align256((size_t)l * L.nsl * 4) : 0;
+    L.as_bytes = g == OS_FP8E4M3 ? align256((size_t)fp8_scale_ld(m) * L.nsl * 4) : 0;
+    L.bs_bytes = (g == OS_FP8E4M3 && !sym) ? align256((size_t)fp8_scale_ld(l) * L.nsl * 4) : 0;
     // the packed-strip buffer is reused by the left and then the right sketch
     const size_t wl = sketch_workspace_bytes(p, m, a_t);
     const size_t wr = sym ? 0 : sketch_workspace_bytes(p, l, b_t);

@@ -60,6 +60,11 @@ struct Tf32Pair {
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// FP8 scales are stored slice-major: entry [t, r] (slice t of z/128, row r) at
+// t * fp8_scale_ld(rows) + r, rows padded to a multiple of 4 so that every
+// slice starts on a 16-byte boundary.
+inline int64_t fp8_scale_ld(int64_t rows) { return (rows + 3) / 4 * 4; }
+
 }  // namespace osk
 
 #define OSK_CUDA_TRY(expr)                                      \

@@ -37,31 +37,66 @@ constexpr int BM = 128;
 constexpr int ROWB = 128;                     // bytes per tile row: one 128-byte swizzle row
 constexpr int kThreads = 192;
 
-// Tile configuration.  kPlanes = 1: BF16 operands (64 K-elements per stage row,
-// tcgen05 kind::f16).  kPlanes = 2: FP32 operands given as two TF32-exact
-// planes hi/lo (32 K-elements per stage row, kind::tf32, three products
-// hi.hi + hi.lo + lo.hi per K step: FP32-level accuracy on the tensor cores).
-template <int kBN, int kStages, int kPlanes>
+// Operand kinds.  Bf16: BF16 operands, 64 K-elements per 128-byte stage row,
+// tcgen05 kind::f16.  Tf32x3: FP32 operands given as two TF32-exact planes
+// hi/lo (32 K-elements per stage row, kind::tf32, three products hi.hi +
+// hi.lo + lo.hi per K step: FP32-level accuracy on the tensor cores).  Fp8:
+// E4M3 operands with one power-of-two scale per (row, 128-element K slice),
+// 128 K-elements per stage row, kind::mxf8f6f4 with UE8M0 block scaling.
+enum class Kind { Bf16, Tf32x3, Fp8 };
+
+template <int kBN, int kStages, Kind kKind>
 struct Cfg {
     static constexpr int BN = kBN;
     static constexpr int STAGES = kStages;
-    static constexpr int PLANES = kPlanes;
-    static constexpr int ELEM = kPlanes == 1 ? 2 : 4;         // bytes per element
+    static constexpr bool FP8 = kKind == Kind::Fp8;
+    static constexpr int PLANES = kKind == Kind::Tf32x3 ? 2 : 1;
+    static constexpr int ELEM = kKind == Kind::Bf16 ? 2 : (kKind == Kind::Tf32x3 ? 4 : 1);   // bytes
     static constexpr int BKE = ROWB / ELEM;                    // K elements per stage
     static constexpr int A_BYTES = BM * ROWB;                  // one plane of A
     static constexpr int B_BYTES = BN * ROWB;                  // one plane of B
-    static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
-    static constexpr int TMEM_COLS = 2 * BN;                   // two accumulators
+    static constexpr int TILE_BYTES = PLANES * (A_BYTES + B_BYTES);
+    // FP8 only: the stage's FP32 scale rows (loaded by TMA) and their UE8M0
+    // copies in the 32 x 16-byte chunk layout that tcgen05.cp moves to TMEM
+    // (chunk c holds rows 128c .. 128c+127: row r at byte 16 (r % 32) + 4 (r / 32)).
+    static constexpr int SA_BYTES = FP8 ? BM * 4 : 0;
+    static constexpr int SB_BYTES = FP8 ? BN * 4 : 0;
+    static constexpr int SFB_CHUNKS = (BN + 127) / 128;
+    static constexpr int CHUNK_BYTES = FP8 ? 512 * (1 + SFB_CHUNKS) : 0;
+    static constexpr int TX_BYTES = TILE_BYTES + SA_BYTES + SB_BYTES;
+    static constexpr int STAGE_BYTES = (TX_BYTES + CHUNK_BYTES + 1023) / 1024 * 1024;
+    // TMEM: two accumulators of BN columns.  FP8 places them 256 columns apart
+    // and keeps one 16-column scale slot per stage in the gaps behind them.
+    static constexpr int ACC_STRIDE = FP8 ? 256 : BN;
+    static constexpr int TMEM_COLS = FP8 ? 512 : 2 * BN;
+    static constexpr int SF_GAP_SLOTS = (256 - BN) / 16;
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
-    static constexpr uint32_t IDESC = kPlanes == 1 ? idesc_bf16_f32(BM, BN) : idesc_tf32_f32(BM, BN);
+    static constexpr uint32_t IDESC = kKind == Kind::Bf16     ? idesc_bf16_f32(BM, BN)
+                                      : kKind == Kind::Tf32x3 ? idesc_tf32_f32(BM, BN)
+                                                              : idesc_mxf8_f32(BM, BN);
     // 3xTF32: the tensor core accumulates each chunk of CHUNK_KB K blocks (K = 256)
     // in TMEM and the epilogue adds the chunks in FP32 registers, so the
-    // accumulation error does not grow with K.  BF16: one chunk per tile.
-    static constexpr int CHUNK_KB = kPlanes == 2 ? 8 : (1 << 30);
+    // accumulation error does not grow with K.  Otherwise one chunk per tile.
+    static constexpr int CHUNK_KB = kKind == Kind::Tf32x3 ? 8 : (1 << 30);
+    static_assert(!FP8 || (BN <= 240 && 2 * SF_GAP_SLOTS >= STAGES), "FP8 scale slots do not fit in TMEM");
+    static_assert(BN % 32 == 0 && BN <= 256, "tile width");
+    static_assert(SMEM <= 232448, "shared memory");
+
+    // TMEM column of stage s's scale slot (A scales at +0..3, B scales at +4..)
+    __host__ __device__ static constexpr uint32_t sf_slot(int s) {
+        return s < SF_GAP_SLOTS ? (uint32_t)(BN + 16 * s) : (uint32_t)(256 + BN + 16 * (s - SF_GAP_SLOTS));
+    }
 };
 
-using CfgBf16 = Cfg<256, 4, 1>;
-using CfgTf32x3 = Cfg<128, 3, 2>;
+using CfgBf16 = Cfg<256, 4, Kind::Bf16>;
+using CfgTf32x3 = Cfg<128, 3, Kind::Tf32x3>;
+using CfgFp8 = Cfg<224, 4, Kind::Fp8>;
+
+// UE8M0 code of a power-of-two FP32 scale in [2^-127, 2^127] (its biased
+// exponent field; 2^-127 is the subnormal with exponent field 0), in all four bytes.
+__device__ __forceinline__ uint32_t ue8m0_x4(float s) {
+    return ((__float_as_uint(s) >> 23) & 0xffu) * 0x01010101u;
+}
 
 struct GemmArgs {
     int64_t m, l;
@@ -86,7 +121,8 @@ __device__ __forceinline__ void tile_coords(const GemmArgs &g, int t, int &tm, i
     tn = in / gm;
 }
 
-// tmap_a0/b0: BF16 operands or the TF32 hi planes; tmap_a1/b1: the lo planes.
+// tmap_a0/b0: BF16 or E4M3 operands, or the TF32 hi planes.  tmap_a1/b1: the
+// TF32 lo planes, or for FP8 the slice-major FP32 scale arrays.
 template <class C>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_constant__ CUtensorMap tmap_b0,
@@ -96,7 +132,8 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *tiles = smem;   // stage s: [A plane 0][A plane 1][B plane 0][B plane 1]
+    // stage s: [A plane 0][A plane 1][B plane 0][B plane 1] | FP8: [A scales][B scales][UE8M0 chunks]
+    uint8_t *tiles = smem;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_BYTES);
     uint64_t *empty = full + STAGES;
     uint64_t *tmem_full = empty + STAGES;
@@ -121,7 +158,7 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
         fence_barrier_init();
         prefetch_tmap(&tmap_a0);
         prefetch_tmap(&tmap_b0);
-        if (C::PLANES == 2) {
+        if (C::PLANES == 2 || C::FP8) {
             prefetch_tmap(&tmap_a1);
             prefetch_tmap(&tmap_b1);
         }
@@ -149,12 +186,17 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                     const int blk = kb / g.kb_per_blk;
                     const int kz = g.kept.idx[blk] * g.b + (kb - blk * g.kb_per_blk) * BKE;
                     uint8_t *st = tiles + stage * C::STAGE_BYTES;
-                    mbar_expect_tx(&full[stage], C::STAGE_BYTES);
+                    mbar_expect_tx(&full[stage], C::TX_BYTES);
                     tma_load_2d(&tmap_a0, &full[stage], st, kz, tm * BM);
                     if (C::PLANES == 2) tma_load_2d(&tmap_a1, &full[stage], st + C::A_BYTES, kz, tm * BM);
                     uint8_t *sb = st + C::PLANES * C::A_BYTES;
                     tma_load_2d(&tmap_b0, &full[stage], sb, kz, tn * BN);
                     if (C::PLANES == 2) tma_load_2d(&tmap_b1, &full[stage], sb + C::B_BYTES, kz, tn * BN);
+                    if (C::FP8) {
+                        // scale rows of K slice kz / 128 (one stage = one slice)
+                        tma_load_2d(&tmap_a1, &full[stage], st + C::TILE_BYTES, tm * BM, kz / 128);
+                        tma_load_2d(&tmap_b1, &full[stage], st + C::TILE_BYTES + C::SA_BYTES, tn * BN, kz / 128);
+                    }
                     issued[stage] = true;
                     issued_phase[stage] = phase;
                     if (++stage == STAGES) stage = 0, phase ^= 1u;
@@ -165,32 +207,65 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                 if (issued[s]) mbar_wait_drain(&full[s], issued_phase[s]);
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int iter = 0;
-            bool ok = true;
-            bool any = false;
-            for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
-              for (int kc = 0; ok && kc < g.num_kb; kc += C::CHUNK_KB, ++iter) {
-                const int kc_end = min(g.num_kb, kc + C::CHUNK_KB);
-                const int a = iter & 1;
-                const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
-                if (!mbar_wait(&tmem_empty[a], aphase ^ 1u, abort)) { ok = false; break; }
+        // ---------------- MMA issuer (lane 0; FP8 uses the whole warp to stage scales) ----------------
+        int stage = 0;
+        uint32_t phase = 0;
+        int iter = 0;
+        bool ok = true;
+        bool any = false;
+        for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
+          for (int kc = 0; ok && kc < g.num_kb; kc += C::CHUNK_KB, ++iter) {
+            const int kc_end = min(g.num_kb, kc + C::CHUNK_KB);
+            const int a = iter & 1;
+            const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+            if (!__all_sync(0xffffffffu, mbar_wait(&tmem_empty[a], aphase ^ 1u, abort))) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d = tmem_base + (uint32_t)(a * C::ACC_STRIDE);
+            for (int kb = kc; kb < kc_end; ++kb) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, abort))) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(a * BN);
-                for (int kb = kc; kb < kc_end; ++kb) {
-                    if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t sa0 = smem_u32(tiles + stage * C::STAGE_BYTES);
-                    const uint32_t sb0 = sa0 + C::PLANES * C::A_BYTES;
+                uint8_t *st = tiles + stage * C::STAGE_BYTES;
+                const uint32_t sa0 = smem_u32(st);
+                const uint32_t sb0 = sa0 + C::PLANES * C::A_BYTES;
+                uint32_t sfa = 0, sfb = 0;
+                if constexpr (C::FP8) {
+                    // FP32 scales -> UE8M0 bytes in the chunk layout; lane i owns chunk row i
+                    const float *fa = reinterpret_cast<const float *>(st + C::TILE_BYTES);
+                    const float *fb = fa + BM;
+                    uint8_t *ch = st + C::TX_BYTES;
+                    *reinterpret_cast<uint4 *>(ch + 16 * lane) =
+                        make_uint4(ue8m0_x4(fa[lane]), ue8m0_x4(fa[lane + 32]), ue8m0_x4(fa[lane + 64]),
+                                   ue8m0_x4(fa[lane + 96]));
+#pragma unroll
+                    for (int c = 0; c < C::SFB_CHUNKS; ++c) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int row = 128 * c + 32 * q + lane;
+                            w[q] = row < BN ? ue8m0_x4(fb[row]) : 0x7f7f7f7fu;
+                        }
+                        *reinterpret_cast<uint4 *>(ch + 512 * (1 + c) + 16 * lane) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                    fence_proxy_async_smem();   // generic-proxy writes -> tcgen05.cp reads
+                    __syncwarp();
+                    sfa = tmem_base + C::sf_slot(stage);
+                    sfb = sfa + 4;
+                    if (lane == 0) {
+                        tmem_cp_32x128b_x4(sfa, sdesc_rows16(smem_u32(ch)));
+#pragma unroll
+                        for (int c = 0; c < C::SFB_CHUNKS; ++c)
+                            tmem_cp_32x128b_x4(sfb + 4 * c, sdesc_rows16(smem_u32(ch + 512 * (1 + c))));
+                    }
+                }
+                if (lane == 0) {
 #pragma unroll
                     for (int kk = 0; kk < ROWB / 32; ++kk) {
                         const uint32_t acc0 = (kb > kc || kk > 0) ? 1u : 0u;
                         const uint64_t ad = sdesc_kmajor_sw128(sa0 + kk * 32);
                         const uint64_t bd = sdesc_kmajor_sw128(sb0 + kk * 32);
-                        if constexpr (C::PLANES == 1) {
+                        if constexpr (C::FP8) {
+                            umma_mxf8(d, ad, bd, C::IDESC, sfa, sfb, acc0);
+                        } else if constexpr (C::PLANES == 1) {
                             umma_f16(d, ad, bd, C::IDESC, acc0);
                         } else {
                             const uint64_t adl = sdesc_kmajor_sw128(sa0 + C::A_BYTES + kk * 32);
@@ -200,19 +275,20 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                             umma_tf32(d, adl, bd, C::IDESC, 1u);      // lo . hi
                         }
                     }
-                    any = true;
                     umma_commit(&empty[stage]);
-                    if (++stage == STAGES) stage = 0, phase ^= 1u;
                 }
-                if (!ok) break;
-                umma_commit(&tmem_full[a]);
-              }
+                __syncwarp();
+                any = true;
+                if (++stage == STAGES) stage = 0, phase ^= 1u;
             }
-            if (!ok && any) {
-                // Drain: wait for the MMAs already issued before freeing TMEM.
-                umma_commit(drain);
-                mbar_wait_drain(drain, 0);
-            }
+            if (!ok) break;
+            if (lane == 0) umma_commit(&tmem_full[a]);
+          }
+        }
+        if (!ok && any && lane == 0) {
+            // Drain: wait for the MMAs already issued before freeing TMEM.
+            umma_commit(drain);
+            mbar_wait_drain(drain, 0);
         }
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
@@ -269,7 +345,8 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
 #pragma unroll
                     for (int ch = 0; ch < BN / 32; ++ch) {
                         uint32_t v[32];
-                        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN + ch * 32), v);
+                        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                               (uint32_t)(a * C::ACC_STRIDE + ch * 32), v);
 #pragma unroll
                         for (int u = 0; u < 32; ++u) total[ch * 32 + u] += __uint_as_float(v[u]);
                     }
@@ -287,7 +364,8 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                 tc_fence_after();
                 for (int ch = 0; ch < BN / 32; ++ch) {
                     uint32_t v[32];
-                    tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN + ch * 32), v);
+                    tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                           (uint32_t)(a * C::ACC_STRIDE + ch * 32), v);
                     store32(r, c0 + ch * 32, reinterpret_cast<const float *>(v));
                 }
                 tc_fence_before();
@@ -328,7 +406,8 @@ PFN_encodeTiled get_encode() {
 
 // 2-D K-major tensor map: rows x cols (cols contiguous), box box_rows x box_cols.
 os_status make_tmap(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int elem_bytes, int64_t rows,
-                    int64_t cols, int64_t ld, int box_rows, int box_cols) {
+                    int64_t cols, int64_t ld, int box_rows, int box_cols,
+                    CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return OS_ERR_CUDA;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -336,7 +415,7 @@ os_status make_tmap(CUtensorMap *map, const void *base, CUtensorMapDataType dt, 
     cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? OS_OK : OS_ERR_INVALID_ARG;
 }
@@ -358,7 +437,8 @@ namespace {
 
 // C = alpha * sum over the listed K blocks of A_blk . B_blk^T (+ beta C).  A is
 // rows x zK, B cols x zK, K-major; for the TF32 configuration A1/B1 are the lo
-// planes (A0/B0 the hi planes).
+// planes (A0/B0 the hi planes); for FP8 they are the FP32 scale arrays
+// (slice-major, fp8_scale_ld(rows) entries per 128-wide K slice).
 template <class C>
 os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0, const void *B1, int64_t ldb,
                     int64_t m, int64_t l, int64_t zK, int32_t blk, const BlockList &kept, float alpha, float beta,
@@ -366,7 +446,7 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
     if (blk % C::BKE != 0) return OS_ERR_UNSUPPORTED;
     if (!aligned16(A0) || !aligned16(B0) || (lda * C::ELEM) % 16 != 0 || (ldb * C::ELEM) % 16 != 0)
         return OS_ERR_INVALID_ARG;
-    if (C::PLANES == 2 && (!aligned16(A1) || !aligned16(B1))) return OS_ERR_INVALID_ARG;
+    if ((C::PLANES == 2 || C::FP8) && (!aligned16(A1) || !aligned16(B1))) return OS_ERR_INVALID_ARG;
     if (zK >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
     GemmArgs g;
     g.m = m;
@@ -382,11 +462,20 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
     g.beta = beta;
     g.C = Cout;
     g.ldc = ldc;
-    const CUtensorMapDataType dt = C::PLANES == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUtensorMapDataType dt = C::FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : C::PLANES == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     CUtensorMap ta0, tb0, ta1, tb1;
     OSK_TRY(make_tmap(&ta0, A0, dt, C::ELEM, m, zK, lda, BM, C::BKE));
     OSK_TRY(make_tmap(&tb0, B0, dt, C::ELEM, l, zK, ldb, C::BN, C::BKE));
-    if (C::PLANES == 2) {
+    if (C::FP8) {
+        // one row of 128 (A) or BN (B) FP32 scales per stage; rows past m / l read as 0
+        const int64_t nsl = zK / 128;
+        OSK_TRY(make_tmap(&ta1, A1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nsl, m, fp8_scale_ld(m), 1, BM,
+                          CU_TENSOR_MAP_SWIZZLE_NONE));
+        OSK_TRY(make_tmap(&tb1, B1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nsl, l, fp8_scale_ld(l), 1, C::BN,
+                          CU_TENSOR_MAP_SWIZZLE_NONE));
+    } else if (C::PLANES == 2) {
         OSK_TRY(make_tmap(&ta1, A1, dt, C::ELEM, m, zK, lda, BM, C::BKE));
         OSK_TRY(make_tmap(&tb1, B1, dt, C::ELEM, l, zK, ldb, C::BN, C::BKE));
     } else {
@@ -416,8 +505,6 @@ os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const floa
                          const void *BtT, int64_t ldbt, const float *b_scales, os_dtype dt, int64_t m,
                          int64_t l, uint64_t mask, float alpha, float beta, float *C, int64_t ldc,
                          cudaStream_t st) {
-    (void)a_scales;
-    (void)b_scales;
     const int64_t z = (int64_t)p->P * p->b;
     const BlockList kept = mask_to_list(mask, p->P);
     if (dt == OS_BF16) return launch_bf16(At, ldat, BtT, ldbt, m, l, z, p->b, kept, alpha, beta, C, ldc, st);
@@ -426,6 +513,11 @@ os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const floa
         const float *a0 = (const float *)At, *b0 = (const float *)BtT;
         return launch_tc<CfgTf32x3>(a0, a0 + m * ldat, ldat, b0, b0 + l * ldbt, ldbt, m, l, z, p->b, kept, alpha,
                                     beta, C, ldc, st);
+    }
+    if (dt == OS_FP8E4M3) {
+        if (!a_scales || !b_scales) return OS_ERR_INVALID_ARG;
+        return launch_tc<CfgFp8>(At, a_scales, ldat, BtT, b_scales, ldbt, m, l, z, p->b, kept, alpha, beta, C, ldc,
+                                 st);
     }
     return OS_ERR_UNSUPPORTED;
 }

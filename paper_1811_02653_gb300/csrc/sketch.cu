@@ -228,7 +228,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                     dst[lane + 32 * k] = r;
                 }
             }
-            if (lane == 0) scales[frow * lds + q0 / 128] = ldexpf(1.f, e);
+            if (lane == 0) scales[(q0 / 128) * lds + frow] = ldexpf(1.f, e);   // slice-major
         } else if constexpr (std::is_same<OutT, Tf32Pair>::value) {
             // FP32 as hi + lo: hi keeps 10 mantissa bits (exact in TF32), lo = x - hi (exact)
             float *d0 = reinterpret_cast<float *>(dst);
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(256) unsketch_rows_kernel(
 
 template <typename InT, typename OutT, int QT, int SLOTS>
 os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int64_t ldx, int64_t F,
-                          const float *col_scale, void *Yt, int64_t ldy, float *scales,
+                          const float *col_scale, void *Yt, int64_t ldy, float *scales, int64_t scale_ld,
                           const BlockList &blocks, cudaStream_t st, int64_t plane_elems = 0) {
     const int z = p->P * p->b;
     const int tpb = (p->b + QT - 1) / QT;
@@ -395,12 +395,12 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
         auto k = sketch_gather_kernel<InT, OutT, QT, true, SLOTS>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
-                                          col_scale, (OutT *)Yt, ldy, scales, z / 128, blocks, tpb, plane_elems);
+                                          col_scale, (OutT *)Yt, ldy, scales, scale_ld, blocks, tpb, plane_elems);
     } else {
         auto k = sketch_gather_kernel<InT, OutT, QT, false, SLOTS>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
-                                          nullptr, (OutT *)Yt, ldy, scales, z / 128, blocks, tpb, plane_elems);
+                                          nullptr, (OutT *)Yt, ldy, scales, scale_ld, blocks, tpb, plane_elems);
     }
     return check_launch();
 }
@@ -410,21 +410,21 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
 // keep the CTAs that run together on few strips.
 template <typename InT>
 os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *col_scale, void *Yt,
-                        os_dtype out_t, int64_t ldy, float *scales, uint64_t block_mask, cudaStream_t st,
-                        int64_t plane_rows = 0) {
+                        os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask,
+                        cudaStream_t st, int64_t plane_rows = 0) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
     const int64_t ss = p->n * kStrip;
     switch (out_t) {
         case OS_F32:
-            return launch_gather_t<InT, float, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, blocks, st);
+            return launch_gather_t<InT, float, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks, st);
         case OS_BF16:
-            return launch_gather_t<InT, __nv_bfloat16, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales,
+            return launch_gather_t<InT, __nv_bfloat16, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
                                                               blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_t<InT, __nv_fp8_e4m3, 128, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales,
+            return launch_gather_t<InT, __nv_fp8_e4m3, 128, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
                                                                blocks, st);
         case OS_TF32X2:
-            return launch_gather_t<InT, Tf32Pair, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, blocks,
+            return launch_gather_t<InT, Tf32Pair, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks,
                                                          st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
@@ -434,20 +434,20 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *co
 // pieces: one address translation per 512 bytes is cheap enough that no
 // packing pass is needed).  F must be a multiple of 128.
 os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, void *Yt, os_dtype out_t,
-                               int64_t ldy, float *scales, uint64_t block_mask, cudaStream_t st,
+                               int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask, cudaStream_t st,
                                int64_t plane_rows = 0) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
     switch (out_t) {
         case OS_F32:
-            return launch_gather_t<float, float, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, blocks, st);
+            return launch_gather_t<float, float, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks, st);
         case OS_BF16:
-            return launch_gather_t<float, __nv_bfloat16, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr,
+            return launch_gather_t<float, __nv_bfloat16, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld,
                                                                 blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_t<float, __nv_fp8_e4m3, 128, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, scales,
+            return launch_gather_t<float, __nv_fp8_e4m3, 128, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, scales, scale_ld,
                                                                  blocks, st);
         case OS_TF32X2:
-            return launch_gather_t<float, Tf32Pair, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, blocks,
+            return launch_gather_t<float, Tf32Pair, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks,
                                                            st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
@@ -519,12 +519,12 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
     void *Xs = ws_base(ws);
     if (a_t == OS_F32) {
         OSK_TRY(launch_pack_cols<float>((const float *)A, lda, m, p->n, (float *)Xs, st));
-        return launch_gather<float>(p, (const float *)Xs, m, col_scale, At, out_t, ldat, scales, block_mask, st,
-                                    m);
+        return launch_gather<float>(p, (const float *)Xs, m, col_scale, At, out_t, ldat, scales, fp8_scale_ld(m),
+                                    block_mask, st, m);
     }
     OSK_TRY(launch_pack_cols<__nv_bfloat16>((const __nv_bfloat16 *)A, lda, m, p->n, (__nv_bfloat16 *)Xs, st));
     return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, m, col_scale, At, out_t, ldat, scales,
-                                        block_mask, st, m);
+                                        fp8_scale_ld(m), block_mask, st, m);
 }
 
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
@@ -542,24 +542,27 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
                         l >= kStrip;
     if (direct) {
         const int64_t lf = l / kStrip * kStrip;
-        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, BtT, out_t, ldbt, scales, block_mask, st, l));
+        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, BtT, out_t, ldbt, scales, fp8_scale_ld(l),
+                                     block_mask, st, l));
         if (lf == l) return OS_OK;
         if (!ws || ws_bytes < sketch_workspace_bytes(p, l - lf, b_t)) return OS_ERR_WORKSPACE;
         float *Xs = (float *)ws_base(ws);
         OSK_TRY(launch_pack_rows<float>((const float *)B + lf, ldb, p->n, l - lf, Xs, st));
         char *yt = (char *)BtT + (size_t)lf * ldbt * dtype_size(out_t);
-        float *sc = scales ? scales + lf * ((int64_t)p->P * p->b / 128) : nullptr;
-        return launch_gather<float>(p, Xs, l - lf, nullptr, yt, out_t, ldbt, sc, block_mask, st, l);
+        float *sc = scales ? scales + lf : nullptr;   // slice-major: the remainder's rows start at lf
+        return launch_gather<float>(p, Xs, l - lf, nullptr, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask, st,
+                                    l);
     }
     if (!ws || ws_bytes < sketch_workspace_bytes(p, l, b_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);
     if (b_t == OS_F32) {
         OSK_TRY(launch_pack_rows<float>((const float *)B, ldb, p->n, l, (float *)Xs, st));
-        return launch_gather<float>(p, (const float *)Xs, l, nullptr, BtT, out_t, ldbt, scales, block_mask, st, l);
+        return launch_gather<float>(p, (const float *)Xs, l, nullptr, BtT, out_t, ldbt, scales, fp8_scale_ld(l),
+                                    block_mask, st, l);
     }
     OSK_TRY(launch_pack_rows<__nv_bfloat16>((const __nv_bfloat16 *)B, ldb, p->n, l, (__nv_bfloat16 *)Xs, st));
     return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, l, nullptr, BtT, out_t, ldbt, scales,
-                                        block_mask, st, l);
+                                        fp8_scale_ld(l), block_mask, st, l);
 }
 
 os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t ldt, uint64_t mask,

@@ -138,6 +138,51 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
         : "memory");
 }
 
+// Instruction descriptor for kind::mxf8f6f4 with block scaling: E4M3 x E4M3
+// -> F32, both K-major, UE8M0 scale factors, scale-factor byte 0 of A and B.
+__host__ __device__ constexpr uint32_t idesc_mxf8_f32(int M, int N) {
+    return (0u << 7)                 // A format E4M3
+           | (0u << 10)              // B format E4M3
+           | ((uint32_t)(N >> 3) << 17)
+           | (1u << 23)              // scale factors are UE8M0
+           | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (+)= (A * SFA) (B * SFB)^T over K = 32: one UE8M0 scale per row and
+// 32-element K block.  The scale-factor operands are TMEM addresses whose
+// layout is the 32-lane x 4-column block written by tmem_cp_32x128b_x4.
+__device__ __forceinline__ void umma_mxf8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t tmem_sfa, uint32_t tmem_sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(tmem_sfa), "r"(tmem_sfb), "r"(accumulate)
+        : "memory");
+}
+
+// Shared-memory descriptor of 32 rows x 16 bytes stored contiguously (no
+// swizzle; 8-row core matrices 128 B apart).
+__device__ __forceinline__ uint64_t sdesc_rows16(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(128u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Copy 32 rows x 16 bytes of shared memory into TMEM lanes 0..31, columns
+// taddr .. taddr+3, replicated into each of the four 32-lane quarters.
+// Ordered before later tcgen05.mma of the same thread.
+__device__ __forceinline__ void tmem_cp_32x128b_x4(uint32_t taddr, uint64_t sdesc) {
+    asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(

@@ -210,7 +210,13 @@ def plan_from_tables(h, sigma, b, N, e, stream=None) -> Plan:
 
 
 def _fp8_scales_shape(rows, z):
-    return (rows, (z + 127) // 128)
+    # slice-major: [t, r] for slice t of z/128 and row r, rows padded to a multiple of 4
+    return ((z + 127) // 128, (rows + 3) // 4 * 4)
+
+
+def fp8_scales_by_row(scales: torch.Tensor, rows: int) -> torch.Tensor:
+    """View of slice-major FP8 scales as rows x (z/128) (entry [r, t])."""
+    return scales[:, :rows].t()
 
 
 def sketch_workspace(p: Plan, free_extent: int, in_dtype=torch.float32) -> int:

@@ -171,3 +171,103 @@ def test_small_workload_fp32_tensor_path(ops):
     C = ops.matmul(p, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), w.mask, "f32")
     h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
     assert oracle.rel_frob(C.cpu().numpy(), oracle.oversketch(A, B, h, s, w.b, w.mask)) <= 1e-5
+
+
+def _fp8_operand(rng, rows, z, emin=-8, emax=8):
+    """Random E4M3 codes (no NaN codes) and slice-major power-of-two scales;
+    returns device codes, device scales and the exact FP64 dequantised matrix."""
+    codes = rng.integers(0, 256, size=(rows, z), dtype=np.uint8)
+    codes[(codes & 0x7F) == 0x7F] = 0x38                       # NaN codes -> 1.0
+    q = torch.from_numpy(codes).cuda().view(torch.float8_e4m3fn)
+    vals = q.float().cpu().numpy().astype(np.float64)
+    nsl, ld = z // 128, (rows + 3) // 4 * 4
+    e = rng.integers(emin, emax + 1, size=(nsl, ld))
+    sc = np.ldexp(1.0, e).astype(np.float32)
+    sc[:, rows:] = np.nan                                      # padding rows must never be read
+    deq = vals * np.repeat(np.ldexp(1.0, e[:, :rows]).T, 128, axis=1)
+    return q, torch.from_numpy(sc).cuda(), deq
+
+
+FP8_CASES = [
+    # m, l, b, N, e, mask
+    (128, 224, 128, 2, 1, 0b011),          # one tile
+    (300, 700, 256, 3, 2, 0b10101),        # ragged m and l, non-contiguous kept blocks
+    (1, 1, 128, 1, 0, 0b1),                # single element
+    (1000, 130, 1024, 2, 1, 0b110),        # K = 2048, l < tile width
+    (129, 449, 128, 4, 1, 0b11110),        # l just past two tile widths
+    (640, 1536, 512, 8, 2, 0b1110111101),  # many tiles (persistent loop, both accumulators)
+]
+
+
+@pytest.mark.parametrize("m,l,b,N,e,mask", FP8_CASES)
+def test_gemm_fp8_parity(ops, m, l, b, N, e, mask):
+    # block-scaled E4M3 x E4M3 products are exact in FP32; only the accumulation rounds
+    rng = np.random.default_rng(m * 17 + l)
+    z = (N + e) * b
+    At, sa, A64 = _fp8_operand(rng, m, z)
+    Bt, sb, B64 = _fp8_operand(rng, l, z)
+    p = ops.plan(max(z, 64), b, N, e, 0)
+    C = ops.gemm_masked(p, At, Bt, mask, a_scales=sa, b_scales=sb).cpu().numpy()
+    ref = oracle.masked_product(A64, B64.T, b, mask)
+    K = bin(mask).count("1") * b
+    absref = oracle.masked_product(np.abs(A64), np.abs(B64).T, b, mask)
+    bound = 2 * K * 2.0 ** -24 * absref + 1e-30
+    assert np.isfinite(C).all()
+    assert (np.abs(C - ref) <= bound).all()
+
+
+def test_gemm_fp8_extreme_scales(ops):
+    # wide scale range, and the smallest UE8M0 scale 2^-127 (a subnormal FP32 value)
+    rng = np.random.default_rng(21)
+    m, l, b, N, e, mask = 256, 224, 128, 2, 0, 0b11
+    z = (N + e) * b
+    At, sa, A64 = _fp8_operand(rng, m, z, -60, 40)
+    Bt, sb, B64 = _fp8_operand(rng, l, z, -40, 40)
+    sa[0, :m] = 2.0 ** -127
+    A64[:, :128] = At.float().cpu().numpy()[:, :128].astype(np.float64) * 2.0 ** -127
+    p = ops.plan(z, b, N, e, 0)
+    C = ops.gemm_masked(p, At, Bt, mask, alpha=1.0, a_scales=sa, b_scales=sb).cpu().numpy()
+    ref = oracle.masked_product(A64, B64.T, b, mask) * 2      # alpha = 1 (masked_product divides by k)
+    absref = oracle.masked_product(np.abs(A64), np.abs(B64).T, b, mask) * 2
+    assert np.isfinite(C).all()
+    assert (np.abs(C - ref) <= 2 * z * 2.0 ** -24 * absref + 1e-37).all()
+
+
+def _fp8_oracle(A, B, w, h, s, cs=None):
+    At_q = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(oracle.sketch_left(A, h, s, w.b, cs)))
+    Bt_q = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(oracle.sketch_right(B, h, s, w.b)))
+    return oracle.masked_product(At_q, Bt_q, w.b, w.mask)
+
+
+def test_small_workload_fp8(ops):
+    w = W.SMALL
+    A, B = w.left(), w.right()
+    p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
+    C = ops.matmul(p, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), w.mask, "fp8")
+    h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+    assert oracle.rel_frob(C.cpu().numpy(), _fp8_oracle(A, B, w, h, s)) <= 1e-3
+
+
+@pytest.mark.parametrize("m,n,l,b,N,e,mask", [(300, 5000, 200, 128, 3, 1, 0b1101),
+                                              (130, 4096, 1000, 1024, 2, 1, 0b011)])
+def test_matmul_fp8_parity(ops, m, n, l, b, N, e, mask):
+    rng = np.random.default_rng(n + 1)
+    A = (rng.standard_normal((m, n)) * np.exp(rng.standard_normal((m, 1)) * 2)).astype(np.float32)
+    B = rng.standard_normal((n, l)).astype(np.float32)
+    w = W.Workload("t", m, n, l, b, N, e, mask)
+    p = ops.plan(n, b, N, e, 5)
+    C = ops.matmul(p, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), mask, "fp8")
+    h, s = oracle.hash_tables(n, b, N, e, 5)
+    assert oracle.rel_frob(C.cpu().numpy(), _fp8_oracle(A, B, w, h, s)) <= 1e-3
+
+
+def test_symmetric_product_fp8(ops):
+    m, n, b, N, e, mask = 200, 6000, 256, 4, 1, 0b11101
+    rng = np.random.default_rng(23)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 0)
+    H = ops.matmul(p, torch.from_numpy(A).cuda(), None, mask, "fp8", symmetric=True).cpu().numpy()
+    h, s = oracle.hash_tables(n, b, N, e, 0)
+    At_q = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(oracle.sketch_left(A, h, s, b)))
+    assert oracle.rel_frob(H, oracle.masked_product(At_q, At_q.T, b, mask)) <= 1e-3
+    assert oracle.rel_frob(H, H.T) <= 1e-6

@@ -151,7 +151,8 @@ def test_sketch_bf16_input(ops):
     assert_fp32_within(BtT.cpu().numpy(), ref_r.T, bd_r.T)
 
 
-@pytest.mark.parametrize("m,n,l,b,N,e", [(256, 4096, 384, 256, 4, 1), (100, 5000, 33, 128, 3, 1)])
+@pytest.mark.parametrize("m,n,l,b,N,e", [(256, 4096, 384, 256, 4, 1), (100, 5000, 33, 128, 3, 1),
+                                         (130, 3000, 301, 128, 2, 1)])   # in-place strips + packed remainder
 def test_sketch_fp8_parity(ops, m, n, l, b, N, e):
     rng = np.random.default_rng(13)
     A = (rng.standard_normal((m, n)) * np.exp(rng.standard_normal((m, 1)) * 3)).astype(np.float32)
@@ -162,8 +163,9 @@ def test_sketch_fp8_parity(ops, m, n, l, b, N, e):
     BtT, sb = ops.sketch_right(p, _dev(B), "fp8")
     ref_l, bd_l = sketch_bounds_left(A, h, s, b)
     ref_r, bd_r = sketch_bounds_right(B, h, s, b)
-    assert_fp8_within(At.float().cpu().numpy(), sa.cpu().numpy(), ref_l, bd_l)
-    assert_fp8_within(BtT.float().cpu().numpy(), sb.cpu().numpy(), ref_r.T, bd_r.T)
+    assert sa.shape == ((N + e) * b // 128, (m + 3) // 4 * 4)      # slice-major scales
+    assert_fp8_within(At.float().cpu().numpy(), ops.fp8_scales_by_row(sa, m).cpu().numpy(), ref_l, bd_l)
+    assert_fp8_within(BtT.float().cpu().numpy(), ops.fp8_scales_by_row(sb, l).cpu().numpy(), ref_r.T, bd_r.T)
 
 
 def test_sketch_argument_errors(ops):
