@@ -10,24 +10,27 @@
 // Right sketch: X = B (n x l), Y^T = B~^T (l x z).  Left sketch: X = A^T,
 // Y^T = A~ (m x z).
 //
-// The operand is first packed strip-major into the workspace: strip s holds
-// X[0..n-1, 32s .. 32s+31] as n contiguous rows of 32 elements (zero-padded
-// past the free extent).  The bucket gather then reads random rows of one
-// 8 MB strip (for FP32, n = 65536) instead of 128-byte pieces of rows spread
-// over the whole matrix; on GB300 the latter runs at a quarter to a half of
-// the L2 gather rate because the translations of a matrix-wide random access
-// pattern do not stay cached.  Packing the left operand is the transpose it
-// needs anyway.
+// The gather reads X in strips of 128 free indices: strip s holds
+// X[0..n-1, 128s .. 128s+127], and a random row of it is one 512-byte piece
+// (FP32).  The left operand (and a right operand whose rows are not 16-byte
+// aligned) is first packed strip-major into the workspace, n contiguous rows
+// of 128 elements per strip, zero-padded past the free extent; packing the
+// left operand is the transpose it needs anyway.  An aligned FP32 right
+// operand is gathered in place.  Whole 512-byte pieces keep the address
+// translations of the random row accesses cheap; 128-byte pieces spread over
+// a 4 GB matrix ran at a quarter to a half of the L2 gather rate on GB300.
 //
 // A gather CTA owns 32 consecutive sketched columns q (whole buckets of one
 // block) and one strip.  Each warp walks the bucket-CSR of its buckets
 // (indices ascending inside a bucket, the same order in every run: no
-// atomics, bitwise reproducible) and gathers 128-byte row pieces with 16-byte
-// loads, accumulating in FP32.  The 32 x 32 tile is transposed through shared
-// memory so that Y^T rows are written contiguously.  FP8 output uses 128-column
-// tiles so that the per-(row, 128-q) power-of-two scale is taken inside one
-// CTA.  CTAs of one strip are adjacent in launch order, so a strip stays in L2
-// while all of its buckets are gathered.
+// atomics, bitwise reproducible) and gathers row pieces with 16-byte loads,
+// accumulating in FP32.  The 32-column x 128-row tile is transposed through
+// shared memory so that Y^T rows are written contiguously.  CTAs of one strip
+// are adjacent in launch order, so a strip stays in L2 while all of its
+// buckets are gathered.  For FP8 output the four CTAs that own the quarters of
+// one 128-column scale slice form a thread-block cluster and combine their
+// per-row maxima through distributed shared memory.
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cstdlib>
 #include <type_traits>
@@ -201,55 +204,70 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
     }
     __syncthreads();
 
-    // Transposed write-out: warp w writes rows f0 + 4w .. 4w+3 of Y^T.
-    constexpr int VPL = QT / 32;         // values per lane per row
-    for (int t = 0; t < TF / kWarps; ++t) {
-        const int ff = warp * (TF / kWarps) + t;
-        const int64_t frow = f0 + ff;
-        if (frow >= F) break;
-        float v[VPL];
+    if constexpr (sizeof(OutT) == 1) {
+        // FP8: cluster rank r holds columns 32r .. 32r+31 of the slice.  Per row:
+        // partial max over 32 columns here, the slice max from all four ranks.
+        static_assert(QT == 32, "FP8 tiles are the quarters of a 128-column scale slice");
+        namespace cg = cooperative_groups;
+        __shared__ float amax_part[TF];
+        cg::cluster_group cl = cg::this_cluster();
+        for (int t = 0; t < TF / kWarps; ++t) {
+            const int ff = warp * (TF / kWarps) + t;
+            float a = fabsf(tile[lane * PITCH + ff]);
 #pragma unroll
-        for (int k = 0; k < VPL; ++k) v[k] = tile[(lane + 32 * k) * PITCH + ff];
-        OutT *dst = Yt + frow * ldy + q0;
-        if constexpr (sizeof(OutT) == 1) {
-            float amax = 0.f;
-#pragma unroll
-            for (int k = 0; k < VPL; ++k)
-                if (q0 + lane + 32 * k < qend) amax = fmaxf(amax, fabsf(v[k]));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-            const int e = fp8_scale_exponent(amax);
-            const float inv = ldexpf(1.f, -e);
-#pragma unroll
-            for (int k = 0; k < VPL; ++k) {
-                const int q = q0 + lane + 32 * k;
-                if (q < qend) {
-                    __nv_fp8_e4m3 r(v[k] * inv);   // RNE, saturating to +-448
-                    dst[lane + 32 * k] = r;
-                }
+            for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+            if (lane == 0) amax_part[ff] = a;
+        }
+        cl.sync();
+        const bool scale_writer = cl.block_rank() == 0 && lane == 0;
+        for (int t = 0; t < TF / kWarps; ++t) {
+            const int ff = warp * (TF / kWarps) + t;
+            const int64_t frow = f0 + ff;
+            float a = lane < 4 ? *cl.map_shared_rank(amax_part + ff, (unsigned)lane) : 0.f;
+            a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
+            a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 2));
+            a = __shfl_sync(0xffffffffu, a, 0);
+            if (frow < F) {
+                const int e = fp8_scale_exponent(a);
+                const float inv = ldexpf(1.f, -e);
+                Yt[frow * ldy + q0 + lane] = __nv_fp8_e4m3(tile[lane * PITCH + ff] * inv);   // RNE, saturating
+                if (scale_writer) scales[(q0 / 128) * lds + frow] = ldexpf(1.f, e);           // slice-major
             }
-            if (lane == 0) scales[(q0 / 128) * lds + frow] = ldexpf(1.f, e);   // slice-major
-        } else if constexpr (std::is_same<OutT, Tf32Pair>::value) {
-            // FP32 as hi + lo: hi keeps 10 mantissa bits (exact in TF32), lo = x - hi (exact)
-            float *d0 = reinterpret_cast<float *>(dst);
+        }
+        cl.sync();   // the partial maxima stay readable until every rank is done
+    } else {
+        // Transposed write-out: warp w writes rows f0 + 16w .. 16w+15 of Y^T.
+        constexpr int VPL = QT / 32;         // values per lane per row
+        for (int t = 0; t < TF / kWarps; ++t) {
+            const int ff = warp * (TF / kWarps) + t;
+            const int64_t frow = f0 + ff;
+            if (frow >= F) break;
+            float v[VPL];
 #pragma unroll
-            for (int k = 0; k < VPL; ++k) {
-                const int q = q0 + lane + 32 * k;
-                if (q < qend) {
-                    const float hi = __uint_as_float(__float_as_uint(v[k]) & 0xffffe000u);
-                    d0[lane + 32 * k] = hi;
-                    d0[plane_elems + lane + 32 * k] = v[k] - hi;
+            for (int k = 0; k < VPL; ++k) v[k] = tile[(lane + 32 * k) * PITCH + ff];
+            OutT *dst = Yt + frow * ldy + q0;
+            if constexpr (std::is_same<OutT, Tf32Pair>::value) {
+                // FP32 as hi + lo: hi keeps 10 mantissa bits (exact in TF32), lo = x - hi (exact)
+                float *d0 = reinterpret_cast<float *>(dst);
+#pragma unroll
+                for (int k = 0; k < VPL; ++k) {
+                    const int q = q0 + lane + 32 * k;
+                    if (q < qend) {
+                        const float hi = __uint_as_float(__float_as_uint(v[k]) & 0xffffe000u);
+                        d0[lane + 32 * k] = hi;
+                        d0[plane_elems + lane + 32 * k] = v[k] - hi;
+                    }
                 }
-            }
-        } else {
+            } else {
 #pragma unroll
-            for (int k = 0; k < VPL; ++k) {
-                const int q = q0 + lane + 32 * k;
-                if (q < qend) {
-                    if constexpr (sizeof(OutT) == 4)
-                        dst[lane + 32 * k] = v[k];
-                    else
-                        dst[lane + 32 * k] = __float2bfloat16_rn(v[k]);
+                for (int k = 0; k < VPL; ++k) {
+                    const int q = q0 + lane + 32 * k;
+                    if (q < qend) {
+                        if constexpr (sizeof(OutT) == 4)
+                            dst[lane + 32 * k] = v[k];
+                        else
+                            dst[lane + 32 * k] = __float2bfloat16_rn(v[k]);
+                    }
                 }
             }
         }
@@ -391,23 +409,36 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
     dim3 grid((unsigned)(tpb * blocks.count), (unsigned)((F + TF - 1) / TF));
     if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;
     const size_t smem = sizeof(float) * QT * (TF + 1);
-    if (col_scale) {
-        auto k = sketch_gather_kernel<InT, OutT, QT, true, SLOTS>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = col_scale ? sketch_gather_kernel<InT, OutT, QT, true, SLOTS>
+                       : sketch_gather_kernel<InT, OutT, QT, false, SLOTS>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (sizeof(OutT) == 1) {
+        // clusters of the 4 CTAs of a 128-column scale slice (b % 128 == 0, so
+        // grid.x is a multiple of 4 and no cluster straddles two blocks)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(kWarps * 32);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 4;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        OSK_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, X, strip_stride, ldx, F, (const uint32_t *)p->pperm,
+                                        (const uint32_t *)p->poffs, p->pstride, p->b, z, col_scale, (OutT *)Yt, ldy,
+                                        scales, scale_ld, blocks, tpb, plane_elems));
+    } else {
         k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
                                           col_scale, (OutT *)Yt, ldy, scales, scale_ld, blocks, tpb, plane_elems);
-    } else {
-        auto k = sketch_gather_kernel<InT, OutT, QT, false, SLOTS>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
-                                          nullptr, (OutT *)Yt, ldy, scales, scale_ld, blocks, tpb, plane_elems);
     }
     return check_launch();
 }
 
-// Gather from an operand packed in 128-wide strips (n rows each).  FP8 output
-// needs whole 128-column scale groups in one CTA; otherwise 32-column tiles
-// keep the CTAs that run together on few strips.
+// Gather from an operand packed in 128-wide strips (n rows each) in tiles of
+// 32 sketched columns, which keeps the CTAs that run together on few strips.
 template <typename InT>
 os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *col_scale, void *Yt,
                         os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask,
@@ -421,7 +452,7 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *co
             return launch_gather_t<InT, __nv_bfloat16, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
                                                               blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_t<InT, __nv_fp8_e4m3, 128, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<InT, __nv_fp8_e4m3, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
                                                                blocks, st);
         case OS_TF32X2:
             return launch_gather_t<InT, Tf32Pair, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks,
@@ -444,7 +475,7 @@ os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64
             return launch_gather_t<float, __nv_bfloat16, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld,
                                                                 blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_t<float, __nv_fp8_e4m3, 128, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<float, __nv_fp8_e4m3, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, scales, scale_ld,
                                                                  blocks, st);
         case OS_TF32X2:
             return launch_gather_t<float, Tf32Pair, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks,
