@@ -7,16 +7,20 @@
 //
 //   C[r, c] = alpha * sum_{j kept} sum_{q < b} At[r, j*b + q] * BtT[c, j*b + q]  (+ beta * C)
 //
-// K block kb (64 wide) of the loop is read by TMA at sketched column
-// kept[kb / (b/64)] * b + (kb mod (b/64)) * 64, so dropped blocks are never
-// loaded.  Both operands are K-major BF16 in the 128-byte swizzled layout.
+// K block kb of the loop (one 128-byte row of K per operand row: 64 BF16, 32
+// TF32 or 128 FP8 values) is read by TMA at sketched column
+// kept[kb / (b/BK)] * b + (kb mod (b/BK)) * BK, so dropped blocks are never
+// loaded.  Operands are K-major in the 128-byte swizzled layout.
 //
-// Kernel organisation (one persistent CTA per SM, 192 threads):
-//   warp 0      TMA producer: 4-stage ring of {A 128x64, B 256x64} tiles
-//   warp 1      TMEM owner + MMA issuer: tcgen05.mma 128x256x16, FP32
-//               accumulators in TMEM, double-buffered (2 x 256 columns)
-//   warps 2..5  epilogue: tcgen05.ld of the 128 x 256 accumulator, alpha /
-//               beta, FP32 stores; overlaps the next tile's MMAs
+// Kernel organisation (one persistent CTA per SM):
+//   warp 0      TMA producer: ring of {A 128 x BK, B BN x BK} stages (FP8 stages
+//               also carry the A and B scale rows of their 128-wide K slice)
+//   warp 1      TMEM owner + MMA issuer: tcgen05.mma 128 x BN per K step, FP32
+//               accumulators in TMEM, double-buffered
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator, alpha / beta, FP32
+//               stores; overlaps the next tile's MMAs
+//   warp 6      (FP8) converts each stage's FP32 scales to UE8M0 bytes in the
+//               layout tcgen05.cp copies to TMEM for the block-scaled MMA
 // Every mbarrier wait is bounded (1 s); on expiry the kernel records
 // OS_ERR_TIMEOUT in the device status word, drains its own copies and MMAs,
 // frees TMEM and returns.
@@ -35,7 +39,6 @@ using namespace tc;
 
 constexpr int BM = 128;
 constexpr int ROWB = 128;                     // bytes per tile row: one 128-byte swizzle row
-constexpr int kThreads = 192;
 
 // Operand kinds.  Bf16: BF16 operands, 64 K-elements per 128-byte stage row,
 // tcgen05 kind::f16.  Tf32x3: FP32 operands given as two TF32-exact planes
@@ -71,6 +74,9 @@ struct Cfg {
     static constexpr int TMEM_COLS = FP8 ? 512 : 2 * BN;
     static constexpr int SF_GAP_SLOTS = (256 - BN) / 16;
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+    // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue; FP8 adds warp 6, which turns
+    // each stage's FP32 scales into UE8M0 chunks ahead of the MMA warp
+    static constexpr int THREADS = FP8 ? 224 : 192;
     static constexpr uint32_t IDESC = kKind == Kind::Bf16     ? idesc_bf16_f32(BM, BN)
                                       : kKind == Kind::Tf32x3 ? idesc_tf32_f32(BM, BN)
                                                               : idesc_mxf8_f32(BM, BN);
@@ -124,7 +130,7 @@ __device__ __forceinline__ void tile_coords(const GemmArgs &g, int t, int &tm, i
 // tmap_a0/b0: BF16 or E4M3 operands, or the TF32 hi planes.  tmap_a1/b1: the
 // TF32 lo planes, or for FP8 the slice-major FP32 scale arrays.
 template <class C>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(C::THREADS, 1)
 gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_constant__ CUtensorMap tmap_b0,
                       const __grid_constant__ CUtensorMap tmap_a1, const __grid_constant__ CUtensorMap tmap_b1,
                       const GemmArgs g) {
@@ -139,7 +145,8 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
     uint64_t *tmem_full = empty + STAGES;
     uint64_t *tmem_empty = tmem_full + 2;
     uint64_t *drain = tmem_empty + 2;
-    uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *sf_ready = drain + 1;    // FP8: stage's scale chunks written (STAGES barriers)
+    uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(sf_ready + STAGES);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_base_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -154,6 +161,7 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             mbar_init(&tmem_empty[a], 128);
         }
         mbar_init(drain, 1);
+        for (int s = 0; s < STAGES; ++s) mbar_init(&sf_ready[s], 1);
         *abort = 0;
         fence_barrier_init();
         prefetch_tmap(&tmap_a0);
@@ -207,7 +215,7 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                 if (issued[s]) mbar_wait_drain(&full[s], issued_phase[s]);
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer (lane 0; FP8 uses the whole warp to stage scales) ----------------
+        // ---------------- MMA issuer (lane 0 issues; the warp waits together) ----------------
         int stage = 0;
         uint32_t phase = 0;
         int iter = 0;
@@ -222,35 +230,20 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             tc_fence_after();
             const uint32_t d = tmem_base + (uint32_t)(a * C::ACC_STRIDE);
             for (int kb = kc; kb < kc_end; ++kb) {
-                if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, abort))) { ok = false; break; }
+                // FP8: the converter warp signals sf_ready once the stage's tiles have
+                // landed and its scale chunks are written
+                uint64_t *ready = C::FP8 ? &sf_ready[stage] : &full[stage];
+                if (!__all_sync(0xffffffffu, mbar_wait(ready, phase, abort))) { ok = false; break; }
                 tc_fence_after();
                 uint8_t *st = tiles + stage * C::STAGE_BYTES;
                 const uint32_t sa0 = smem_u32(st);
                 const uint32_t sb0 = sa0 + C::PLANES * C::A_BYTES;
                 uint32_t sfa = 0, sfb = 0;
                 if constexpr (C::FP8) {
-                    // FP32 scales -> UE8M0 bytes in the chunk layout; lane i owns chunk row i
-                    const float *fa = reinterpret_cast<const float *>(st + C::TILE_BYTES);
-                    const float *fb = fa + BM;
-                    uint8_t *ch = st + C::TX_BYTES;
-                    *reinterpret_cast<uint4 *>(ch + 16 * lane) =
-                        make_uint4(ue8m0_x4(fa[lane]), ue8m0_x4(fa[lane + 32]), ue8m0_x4(fa[lane + 64]),
-                                   ue8m0_x4(fa[lane + 96]));
-#pragma unroll
-                    for (int c = 0; c < C::SFB_CHUNKS; ++c) {
-                        uint32_t w[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int row = 128 * c + 32 * q + lane;
-                            w[q] = row < BN ? ue8m0_x4(fb[row]) : 0x7f7f7f7fu;
-                        }
-                        *reinterpret_cast<uint4 *>(ch + 512 * (1 + c) + 16 * lane) = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
-                    fence_proxy_async_smem();   // generic-proxy writes -> tcgen05.cp reads
-                    __syncwarp();
                     sfa = tmem_base + C::sf_slot(stage);
                     sfb = sfa + 4;
                     if (lane == 0) {
+                        uint8_t *ch = st + C::TX_BYTES;
                         tmem_cp_32x128b_x4(sfa, sdesc_rows16(smem_u32(ch)));
 #pragma unroll
                         for (int c = 0; c < C::SFB_CHUNKS; ++c)
@@ -289,6 +282,40 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             // Drain: wait for the MMAs already issued before freeing TMEM.
             umma_commit(drain);
             mbar_wait_drain(drain, 0);
+        }
+    } else if (warp == 6) {
+        // ---------------- FP8 scale converter ----------------
+        // FP32 scales -> UE8M0 bytes in the chunk layout; lane i owns chunk row i
+        if constexpr (C::FP8) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
+                for (int kb = 0; kb < g.num_kb; ++kb) {
+                    if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, abort))) { ok = false; break; }
+                    uint8_t *st = tiles + stage * C::STAGE_BYTES;
+                    const float *fa = reinterpret_cast<const float *>(st + C::TILE_BYTES);
+                    const float *fb = fa + BM;
+                    uint8_t *ch = st + C::TX_BYTES;
+                    *reinterpret_cast<uint4 *>(ch + 16 * lane) =
+                        make_uint4(ue8m0_x4(fa[lane]), ue8m0_x4(fa[lane + 32]), ue8m0_x4(fa[lane + 64]),
+                                   ue8m0_x4(fa[lane + 96]));
+#pragma unroll
+                    for (int c = 0; c < C::SFB_CHUNKS; ++c) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int row = 128 * c + 32 * q + lane;
+                            w[q] = row < BN ? ue8m0_x4(fb[row]) : 0x7f7f7f7fu;
+                        }
+                        *reinterpret_cast<uint4 *>(ch + 512 * (1 + c) + 16 * lane) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                    fence_proxy_async_smem();   // generic-proxy writes -> tcgen05.cp reads
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sf_ready[stage]);
+                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                }
+            }
         }
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
@@ -489,7 +516,7 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
         attr_set = true;
     }
     const int grid = g.num_tiles < num_sms() ? g.num_tiles : num_sms();
-    gemm_masked_tc_kernel<C><<<grid, kThreads, C::SMEM, st>>>(ta0, tb0, ta1, tb1, g);
+    gemm_masked_tc_kernel<C><<<grid, C::THREADS, C::SMEM, st>>>(ta0, tb0, ta1, tb1, g);
     return check_launch();
 }
 
