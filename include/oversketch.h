@@ -300,6 +300,64 @@ OS_API os_status oversketch_frob(const float *X, int64_t ldx, const float *Y, in
  */
 OS_API os_status oversketch_device_status(void *stream, int32_t *status, int32_t reset);
 
+/* -------------------------------------------------------------------------
+ * Batches of independent products (Alg. 3's blocks are independent jobs;
+ * here so are whole products).  Product p is
+ *   C_p = (1/k_p) (A_p S_p,sel)(S_p,sel^T B_p),  k_p = popcount(mask_p),
+ * with its own sizes, plan and mask; the GEMM runs in BF16 with FP32
+ * accumulation, like oversketch_matmul with gemm_dtype OS_BF16.
+ *
+ * oversketch_batch_create fixes the products (sizes, pointers, plans and
+ * masks are captured: later runs read A_p, B_p and write C_p at the same
+ * addresses) and records one CUDA graph: the sketches of the products spread
+ * over W parallel branches (each with one packing workspace slot), then one
+ * persistent tensor-core launch over the tiles of all products, longest K
+ * first.  It allocates the sketched operands (BF16, (m_p + l_p) * z_p
+ * elements per product) and W workspace slots of the largest single-product
+ * packing size, W <= workspace_limit / slot (0: 16 GiB).  tune != 0 times a
+ * few (W, tile width) choices on `stream` (running the products several
+ * times) and keeps the fastest; tune == 0 takes W = min(8, ...) and 256-wide
+ * tiles.  Synchronous; call it outside any stream capture.
+ *   problems: host array of count (1..1024) descriptors; A_p, B_p device
+ *     row-major in a_t / b_t (OS_F32 or OS_BF16), C_p device FP32; every plan
+ *     on the current device with b % 64 == 0; m_p, n_p, l_p >= 1.
+ *   gemm_dtype: OS_BF16 (others: OS_ERR_DTYPE).
+ * oversketch_batch_run launches the graph on `stream` (stream-ordered, on
+ *   the device the batch was created on).  Runs of one batch must not overlap.
+ * oversketch_batch_info: what the batch holds and chose.
+ * Errors: OS_ERR_INVALID_ARG, OS_ERR_MASK, OS_ERR_DTYPE, OS_ERR_UNSUPPORTED,
+ *   OS_ERR_WORKSPACE (one product's packing slot exceeds workspace_limit),
+ *   OS_ERR_CUDA.
+ */
+typedef struct {
+    int64_t m, n, l;
+    const void *A; int64_t lda;      /* m x n */
+    const void *B; int64_t ldb;      /* n x l */
+    float *C; int64_t ldc;           /* m x l, FP32 */
+    oversketch_plan_t plan;          /* dimension n */
+    uint64_t mask;                   /* kept blocks */
+} os_problem;
+
+typedef struct oversketch_batch_s *oversketch_batch_t;
+
+typedef struct {
+    int32_t count;                   /* products */
+    int32_t branches;                /* parallel sketch branches W */
+    int32_t tile_n;                  /* GEMM tile width (128 x tile_n tiles) */
+    int32_t total_tiles;             /* tiles of the grouped GEMM launch */
+    int32_t kernel_launches;         /* kernels per run */
+    size_t operand_bytes;            /* sketched operands held */
+    size_t workspace_bytes;          /* packing slots held */
+    float tuned_ms;                  /* median run time of the choice when tuned, else 0 */
+} os_batch_info;
+
+OS_API os_status oversketch_batch_create(const os_problem *problems, int32_t count, os_dtype a_t,
+                                         os_dtype b_t, os_dtype gemm_dtype, size_t workspace_limit,
+                                         int32_t tune, void *stream, oversketch_batch_t *batch);
+OS_API os_status oversketch_batch_run(oversketch_batch_t batch, void *stream);
+OS_API os_status oversketch_batch_info(oversketch_batch_t batch, os_batch_info *info);
+OS_API os_status oversketch_batch_destroy(oversketch_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

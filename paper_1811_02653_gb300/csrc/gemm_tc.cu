@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "group.cuh"
 #include "tc_common.cuh"
 
 namespace osk {
@@ -95,6 +96,7 @@ struct Cfg {
 };
 
 using CfgBf16 = Cfg<256, 4, Kind::Bf16>;
+using CfgBf16N128 = Cfg<128, 6, Kind::Bf16>;   // narrower tiles for grouped launches of small products
 using CfgTf32x3 = Cfg<128, 3, Kind::Tf32x3>;
 using CfgFp8 = Cfg<224, 4, Kind::Fp8>;
 
@@ -105,6 +107,8 @@ __device__ __forceinline__ uint32_t ue8m0_x4(float s) {
 }
 
 struct GemmArgs {
+    const GroupProblem *group;   // grouped launch: product descriptors (else null)
+    int32_t group_count;
     int64_t m, l;
     int32_t b;            // block width (multiple of the stage's K elements)
     int32_t kb_per_blk;   // b / BKE
@@ -116,26 +120,51 @@ struct GemmArgs {
     BlockList kept;
 };
 
-__device__ __forceinline__ void tile_coords(const GemmArgs &g, int t, int &tm, int &tn) {
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
     // Groups of 16 m-tiles: consecutive tiles share A panels and nearby B panels.
     constexpr int G = 16;
-    const int group = t / (G * g.tiles_n);
+    const int group = t / (G * tiles_n);
     const int first_m = group * G;
-    const int gm = min(G, g.tiles_m - first_m);
-    const int in = t - group * G * g.tiles_n;
+    const int gm = min(G, tiles_m - first_m);
+    const int in = t - group * G * tiles_n;
     tm = first_m + in % gm;
     tn = in / gm;
 }
 
+// Product owning global tile t of a grouped launch: the last p with begin[p] <= t.
+__device__ __forceinline__ int find_problem(const int32_t *begin, int count, int t) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Everything one role needs to know about a tile.
+struct TileJob {
+    const CUtensorMap *ta, *tb;
+    const int32_t *kept;          // kept block indices
+    int tm, tn;
+    int num_kb, kb_per_blk, b;
+    float *C;
+    int64_t m, l, ldc;
+    float alpha, beta;
+};
+
 // tmap_a0/b0: BF16 or E4M3 operands, or the TF32 hi planes.  tmap_a1/b1: the
-// TF32 lo planes, or for FP8 the slice-major FP32 scale arrays.
-template <class C>
+// TF32 lo planes, or for FP8 the slice-major FP32 scale arrays.  GROUPED: the
+// tiles of g.group_count products (descriptors g.group, tile_begin ascending)
+// share one persistent launch; the tensor maps come from the descriptors.
+template <class C, bool GROUPED>
 __global__ void __launch_bounds__(C::THREADS, 1)
 gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_constant__ CUtensorMap tmap_b0,
                       const __grid_constant__ CUtensorMap tmap_a1, const __grid_constant__ CUtensorMap tmap_b1,
                       const GemmArgs g) {
     constexpr int STAGES = C::STAGES, BN = C::BN, BKE = C::BKE;
+    static_assert(!GROUPED || C::PLANES == 1 && !C::FP8, "grouped launches take BF16 operands");
     extern __shared__ uint8_t smem_raw[];
+    __shared__ int32_t s_begin[GROUPED ? kMaxGroup : 1];   // first tile of each product
     // 1024-byte alignment for the swizzled tiles
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     // stage s: [A plane 0][A plane 1][B plane 0][B plane 1] | FP8: [A scales][B scales][UE8M0 chunks]
@@ -151,6 +180,8 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    if constexpr (GROUPED)
+        for (int i = threadIdx.x; i < g.group_count; i += blockDim.x) s_begin[i] = g.group[i].tile_begin;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -164,11 +195,13 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
         for (int s = 0; s < STAGES; ++s) mbar_init(&sf_ready[s], 1);
         *abort = 0;
         fence_barrier_init();
-        prefetch_tmap(&tmap_a0);
-        prefetch_tmap(&tmap_b0);
-        if (C::PLANES == 2 || C::FP8) {
-            prefetch_tmap(&tmap_a1);
-            prefetch_tmap(&tmap_b1);
+        if constexpr (!GROUPED) {
+            prefetch_tmap(&tmap_a0);
+            prefetch_tmap(&tmap_b0);
+            if (C::PLANES == 2 || C::FP8) {
+                prefetch_tmap(&tmap_a1);
+                prefetch_tmap(&tmap_b1);
+            }
         }
     }
     if (warp == 1) tmem_alloc(tmem_base_slot, C::TMEM_COLS);
@@ -176,6 +209,47 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_base_slot;
+
+    // The tile's product, coordinates and epilogue parameters.
+    auto job = [&](int t) {
+        TileJob j;
+        if constexpr (GROUPED) {
+            const int p = find_problem(s_begin, g.group_count, t);
+            const GroupProblem *P = g.group + p;
+            tile_coords(t - s_begin[p], P->tiles_m, P->tiles_n, j.tm, j.tn);
+            j.ta = &P->ta;
+            j.tb = &P->tb;
+            j.kept = P->kept.idx;
+            j.num_kb = P->num_kb;
+            j.kb_per_blk = P->kb_per_blk;
+            j.b = P->b;
+            j.C = P->C;
+            j.m = P->m;
+            j.l = P->l;
+            j.ldc = P->ldc;
+            j.alpha = P->alpha;
+            j.beta = P->beta;
+        } else {
+            tile_coords(t, g.tiles_m, g.tiles_n, j.tm, j.tn);
+            j.ta = &tmap_a0;
+            j.tb = &tmap_b0;
+            j.kept = nullptr;             // read g.kept directly (no copy of the parameter)
+            j.num_kb = g.num_kb;
+            j.kb_per_blk = g.kb_per_blk;
+            j.b = g.b;
+            j.C = g.C;
+            j.m = g.m;
+            j.l = g.l;
+            j.ldc = g.ldc;
+            j.alpha = g.alpha;
+            j.beta = g.beta;
+        }
+        return j;
+    };
+    auto num_kb_of = [&](int t) -> int {
+        if constexpr (GROUPED) return g.group[find_problem(s_begin, g.group_count, t)].num_kb;
+        else return g.num_kb;
+    };
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -187,23 +261,23 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             for (int s = 0; s < STAGES; ++s) issued[s] = false, issued_phase[s] = 0;
             bool ok = true;
             for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
-                int tm, tn;
-                tile_coords(g, t, tm, tn);
-                for (int kb = 0; kb < g.num_kb; ++kb) {
+                const TileJob j = job(t);
+                for (int kb = 0; kb < j.num_kb; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
-                    const int blk = kb / g.kb_per_blk;
-                    const int kz = g.kept.idx[blk] * g.b + (kb - blk * g.kb_per_blk) * BKE;
+                    const int blk = kb / j.kb_per_blk;
+                    const int kidx = GROUPED ? j.kept[blk] : g.kept.idx[blk];
+                    const int kz = kidx * j.b + (kb - blk * j.kb_per_blk) * BKE;
                     uint8_t *st = tiles + stage * C::STAGE_BYTES;
                     mbar_expect_tx(&full[stage], C::TX_BYTES);
-                    tma_load_2d(&tmap_a0, &full[stage], st, kz, tm * BM);
-                    if (C::PLANES == 2) tma_load_2d(&tmap_a1, &full[stage], st + C::A_BYTES, kz, tm * BM);
+                    tma_load_2d(j.ta, &full[stage], st, kz, j.tm * BM);
+                    if (C::PLANES == 2) tma_load_2d(&tmap_a1, &full[stage], st + C::A_BYTES, kz, j.tm * BM);
                     uint8_t *sb = st + C::PLANES * C::A_BYTES;
-                    tma_load_2d(&tmap_b0, &full[stage], sb, kz, tn * BN);
-                    if (C::PLANES == 2) tma_load_2d(&tmap_b1, &full[stage], sb + C::B_BYTES, kz, tn * BN);
+                    tma_load_2d(j.tb, &full[stage], sb, kz, j.tn * BN);
+                    if (C::PLANES == 2) tma_load_2d(&tmap_b1, &full[stage], sb + C::B_BYTES, kz, j.tn * BN);
                     if (C::FP8) {
                         // scale rows of K slice kz / 128 (one stage = one slice)
-                        tma_load_2d(&tmap_a1, &full[stage], st + C::TILE_BYTES, tm * BM, kz / 128);
-                        tma_load_2d(&tmap_b1, &full[stage], st + C::TILE_BYTES + C::SA_BYTES, tn * BN, kz / 128);
+                        tma_load_2d(&tmap_a1, &full[stage], st + C::TILE_BYTES, j.tm * BM, kz / 128);
+                        tma_load_2d(&tmap_b1, &full[stage], st + C::TILE_BYTES + C::SA_BYTES, j.tn * BN, kz / 128);
                     }
                     issued[stage] = true;
                     issued_phase[stage] = phase;
@@ -222,8 +296,9 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
         bool ok = true;
         bool any = false;
         for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
-          for (int kc = 0; ok && kc < g.num_kb; kc += C::CHUNK_KB, ++iter) {
-            const int kc_end = min(g.num_kb, kc + C::CHUNK_KB);
+          const int num_kb = num_kb_of(t);
+          for (int kc = 0; ok && kc < num_kb; kc += C::CHUNK_KB, ++iter) {
+            const int kc_end = min(num_kb, kc + C::CHUNK_KB);
             const int a = iter & 1;
             const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
             if (!__all_sync(0xffffffffu, mbar_wait(&tmem_empty[a], aphase ^ 1u, abort))) { ok = false; break; }
@@ -291,7 +366,8 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             uint32_t phase = 0;
             bool ok = true;
             for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
-                for (int kb = 0; kb < g.num_kb; ++kb) {
+                const int num_kb = num_kb_of(t);
+                for (int kb = 0; kb < num_kb; ++kb) {
                     if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, abort))) { ok = false; break; }
                     uint8_t *st = tiles + stage * C::STAGE_BYTES;
                     const float *fa = reinterpret_cast<const float *>(st + C::TILE_BYTES);
@@ -322,31 +398,30 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
         const int quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
         const int row_in_tile = quarter * 32 + lane;
         int iter = 0;
-        const bool vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15u) == 0) && (g.ldc % 4 == 0);
         // FP32 store of 32 consecutive values of row r starting at column cbase
-        auto store32 = [&](int64_t r, int64_t cbase, const float *val) {
-            if (r >= g.m) return;
-            float *dst = g.C + r * g.ldc + cbase;
-            if (vec_ok && cbase + 32 <= g.l) {
+        auto store32 = [&](const TileJob &j, bool vec_ok, int64_t r, int64_t cbase, const float *val) {
+            if (r >= j.m) return;
+            float *dst = j.C + r * j.ldc + cbase;
+            if (vec_ok && cbase + 32 <= j.l) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    float4 o = make_float4(g.alpha * val[4 * u + 0], g.alpha * val[4 * u + 1],
-                                           g.alpha * val[4 * u + 2], g.alpha * val[4 * u + 3]);
-                    if (g.beta != 0.f) {
+                    float4 o = make_float4(j.alpha * val[4 * u + 0], j.alpha * val[4 * u + 1],
+                                           j.alpha * val[4 * u + 2], j.alpha * val[4 * u + 3]);
+                    if (j.beta != 0.f) {
                         const float4 old = *reinterpret_cast<const float4 *>(dst + 4 * u);
-                        o.x = fmaf(g.beta, old.x, o.x);
-                        o.y = fmaf(g.beta, old.y, o.y);
-                        o.z = fmaf(g.beta, old.z, o.z);
-                        o.w = fmaf(g.beta, old.w, o.w);
+                        o.x = fmaf(j.beta, old.x, o.x);
+                        o.y = fmaf(j.beta, old.y, o.y);
+                        o.z = fmaf(j.beta, old.z, o.z);
+                        o.w = fmaf(j.beta, old.w, o.w);
                     }
                     *reinterpret_cast<float4 *>(dst + 4 * u) = o;
                 }
             } else {
 #pragma unroll
                 for (int u = 0; u < 32; ++u) {
-                    if (cbase + u < g.l) {
-                        float o = g.alpha * val[u];
-                        if (g.beta != 0.f) o = fmaf(g.beta, dst[u], o);
+                    if (cbase + u < j.l) {
+                        float o = j.alpha * val[u];
+                        if (j.beta != 0.f) o = fmaf(j.beta, dst[u], o);
                         dst[u] = o;
                     }
                 }
@@ -354,16 +429,16 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
         };
         bool ok = true;
         for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
-            int tm, tn;
-            tile_coords(g, t, tm, tn);
-            const int64_t r = (int64_t)tm * BM + row_in_tile;
-            const int64_t c0 = (int64_t)tn * BN;
+            const TileJob j = job(t);
+            const bool vec_ok = ((reinterpret_cast<uintptr_t>(j.C) & 15u) == 0) && (j.ldc % 4 == 0);
+            const int64_t r = (int64_t)j.tm * BM + row_in_tile;
+            const int64_t c0 = (int64_t)j.tn * BN;
             if constexpr (C::CHUNK_KB < (1 << 30)) {
                 // chunked accumulation: running FP32 sum of the tile row in registers
                 float total[BN];
 #pragma unroll
                 for (int u = 0; u < BN; ++u) total[u] = 0.f;
-                for (int kc = 0; kc < g.num_kb; kc += C::CHUNK_KB, ++iter) {
+                for (int kc = 0; kc < j.num_kb; kc += C::CHUNK_KB, ++iter) {
                     const int a = iter & 1;
                     const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
                     // warp-uniform decision: tcgen05.ld below is a .sync.aligned instruction
@@ -382,7 +457,7 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                 }
                 if (!ok) break;
 #pragma unroll
-                for (int ch = 0; ch < BN / 32; ++ch) store32(r, c0 + ch * 32, total + ch * 32);
+                for (int ch = 0; ch < BN / 32; ++ch) store32(j, vec_ok, r, c0 + ch * 32, total + ch * 32);
             } else {
                 const int a = iter & 1;
                 const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
@@ -393,7 +468,7 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
                                            (uint32_t)(a * C::ACC_STRIDE + ch * 32), v);
-                    store32(r, c0 + ch * 32, reinterpret_cast<const float *>(v));
+                    store32(j, vec_ok, r, c0 + ch * 32, reinterpret_cast<const float *>(v));
                 }
                 tc_fence_before();
                 mbar_arrive(&tmem_empty[a]);
@@ -476,6 +551,8 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
     if ((C::PLANES == 2 || C::FP8) && (!aligned16(A1) || !aligned16(B1))) return OS_ERR_INVALID_ARG;
     if (zK >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
     GemmArgs g;
+    g.group = nullptr;
+    g.group_count = 0;
     g.m = m;
     g.l = l;
     g.b = blk;
@@ -511,12 +588,12 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
     }
     static bool attr_set = false;
     if (!attr_set) {
-        OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_masked_tc_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)C::SMEM));
+        OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_masked_tc_kernel<C, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
         attr_set = true;
     }
     const int grid = g.num_tiles < num_sms() ? g.num_tiles : num_sms();
-    gemm_masked_tc_kernel<C><<<grid, C::THREADS, C::SMEM, st>>>(ta0, tb0, ta1, tb1, g);
+    gemm_masked_tc_kernel<C, false><<<grid, C::THREADS, C::SMEM, st>>>(ta0, tb0, ta1, tb1, g);
     return check_launch();
 }
 
@@ -547,6 +624,70 @@ os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const floa
                                  st);
     }
     return OS_ERR_UNSUPPORTED;
+}
+
+os_status group_problem_bf16(GroupProblem *gp, GroupTile tile, const void *A, int64_t lda, const void *B,
+                             int64_t ldb, int64_t m, int64_t l, int64_t zK, int32_t blk, const BlockList &kept,
+                             float alpha, float beta, float *C, int64_t ldc) {
+    const int BN = tile == kGroupBN256 ? CfgBf16::BN : CfgBf16N128::BN;
+    constexpr int BKE = CfgBf16::BKE;
+    if (m <= 0 || l <= 0 || kept.count <= 0) return OS_ERR_INVALID_ARG;
+    if (blk % BKE != 0) return OS_ERR_UNSUPPORTED;
+    if (!aligned16(A) || !aligned16(B) || (lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0) return OS_ERR_INVALID_ARG;
+    if (zK >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
+    std::memset(gp, 0, sizeof(*gp));
+    OSK_TRY(make_tmap(&gp->ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, zK, lda, BM, BKE));
+    OSK_TRY(make_tmap(&gp->tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, zK, ldb, BN, BKE));
+    gp->C = C;
+    gp->m = m;
+    gp->l = l;
+    gp->ldc = ldc;
+    gp->alpha = alpha;
+    gp->beta = beta;
+    gp->b = blk;
+    gp->kb_per_blk = blk / BKE;
+    gp->num_kb = kept.count * gp->kb_per_blk;
+    gp->tiles_m = (int32_t)((m + BM - 1) / BM);
+    gp->tiles_n = (int32_t)((l + BN - 1) / BN);
+    gp->tile_begin = 0;
+    gp->kept = kept;
+    return OS_OK;
+}
+
+namespace {
+template <class C>
+os_status prepare_grouped() {
+    OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_masked_tc_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)C::SMEM));
+    return OS_OK;
+}
+
+template <class C>
+os_status launch_grouped(const GroupProblem *probs, int32_t count, int32_t total_tiles, cudaStream_t st) {
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.group = probs;
+    g.group_count = count;
+    g.num_tiles = total_tiles;
+    // the per-product tensor maps are read from global memory; these are placeholders
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    const int grid = total_tiles < num_sms() ? total_tiles : num_sms();
+    gemm_masked_tc_kernel<C, true><<<grid, C::THREADS, C::SMEM, st>>>(dummy, dummy, dummy, dummy, g);
+    return check_launch();
+}
+}  // namespace
+
+os_status gemm_grouped_prepare() {
+    OSK_TRY(prepare_grouped<CfgBf16>());
+    return prepare_grouped<CfgBf16N128>();
+}
+
+os_status gemm_grouped_bf16(const GroupProblem *probs, int32_t count, int32_t total_tiles, GroupTile tile,
+                            cudaStream_t st) {
+    if (!probs || count <= 0 || count > kMaxGroup || total_tiles <= 0) return OS_ERR_INVALID_ARG;
+    if (tile == kGroupBN256) return launch_grouped<CfgBf16>(probs, count, total_tiles, st);
+    return launch_grouped<CfgBf16N128>(probs, count, total_tiles, st);
 }
 
 }  // namespace osk

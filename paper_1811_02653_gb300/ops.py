@@ -41,6 +41,21 @@ class _Opts(ctypes.Structure):
                 ("symmetric", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("l", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64),
+                ("plan", ctypes.c_void_p), ("mask", ctypes.c_uint64)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("branches", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+                ("total_tiles", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("operand_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
+                ("tuned_ms", ctypes.c_float)]
+
+
 def load_library(path: str | None = None):
     """Load liboversketch.so (raises if it is missing: there is no fallback)."""
     global _lib
@@ -78,6 +93,10 @@ def load_library(path: str | None = None):
             "oversketch_gemm_bf16": (st, [vp, i64, vp, i64, i64, i64, i64, f32, f32, vp, i64, vp]),
             "oversketch_select_transpose": (st, [vp, st, i64, i64, i64, u64, i32, vp, st, i64, vp]),
             "oversketch_cast": (st, [vp, st, i64, i64, i64, vp, st, i64, vp]),
+            "oversketch_batch_create": (st, [ctypes.POINTER(_Problem), i32, st, st, st, sz, i32, vp, pp]),
+            "oversketch_batch_run": (st, [vp, vp]),
+            "oversketch_batch_info": (st, [vp, ctypes.POINTER(_BatchInfo)]),
+            "oversketch_batch_destroy": (st, [vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -98,7 +117,9 @@ def _sigs_names():
             "oversketch_sketch_right", "oversketch_gemm_masked", "oversketch_workspace_size",
             "oversketch_matmul", "oversketch_unsketch_cols", "oversketch_unsketch_rows",
             "oversketch_frob", "oversketch_device_status", "oversketch_sketch_left_noalloc",
-            "oversketch_gemm_bf16", "oversketch_select_transpose", "oversketch_cast"]
+            "oversketch_gemm_bf16", "oversketch_select_transpose", "oversketch_cast",
+            "oversketch_batch_create", "oversketch_batch_run", "oversketch_batch_info",
+            "oversketch_batch_destroy"]
 
 
 def _check(status: int, what: str):
@@ -428,3 +449,53 @@ def cast(X, out_dtype, out=None, stream=None):
     _check(load_library().oversketch_cast(_ptr(X), _dt(X), rows, cols, ldx, _ptr(out), od, out.stride(0),
                                           _stream(stream)), "oversketch_cast")
     return out
+
+
+class Batch:
+    """Many independent products run as one CUDA graph (oversketch_batch_*).
+
+    ``problems``: list of (A, B, C, plan, mask) with A (m x n) and B (n x l)
+    row-major CUDA tensors (FP32 or BF16, one dtype per side for the whole
+    batch) and C (m x l) FP32.  The tensors are captured by address: keep
+    them alive and in place while the batch exists.
+    """
+
+    def __init__(self, problems, gemm_dtype="bf16", workspace_limit=0, tune=False, stream=None):
+        lib = load_library()
+        arr = (_Problem * len(problems))()
+        a_t = b_t = None
+        self._keep = []
+        for i, (A, B, C, plan, mask) in enumerate(problems):
+            m, n = A.shape
+            l = B.shape[1]
+            arr[i] = _Problem(m, n, l, A.data_ptr(), _rowmajor(A, "A"), B.data_ptr(), _rowmajor(B, "B"),
+                              C.data_ptr(), _rowmajor(C, "C"), plan.handle.value, mask)
+            a_t = _dt(A) if a_t is None else a_t
+            b_t = _dt(B) if b_t is None else b_t
+            if _dt(A) != a_t or _dt(B) != b_t:
+                raise OverSketchError("Batch: one dtype per operand side")
+            self._keep.append((A, B, C, plan))
+        h = ctypes.c_void_p()
+        _check(lib.oversketch_batch_create(arr, len(problems), a_t, b_t, _dtype_code(gemm_dtype),
+                                           workspace_limit, 1 if tune else 0, _stream(stream), ctypes.byref(h)),
+               "oversketch_batch_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(load_library().oversketch_batch_run(self.handle, _stream(stream)), "oversketch_batch_run")
+
+    def info(self) -> dict:
+        inf = _BatchInfo()
+        _check(load_library().oversketch_batch_info(self.handle, ctypes.byref(inf)), "oversketch_batch_info")
+        return {f: getattr(inf, f) for f, _ in _BatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().oversketch_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
