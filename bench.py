@@ -424,6 +424,255 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# the other workloads (--workload): parity cases of the suite, measured the same way
+# ----------------------------------------------------------------------------
+
+def _time_phases(phases, steps, warmup, world):
+    """W untimed warm-up steps, then K timed steps bracketed by a barrier and a
+    synchronize, with one CUDA event per phase boundary on the launching stream.
+    Returns (ms per step (max over ranks), {phase: mean ms}, clocks)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        for _, fn in phases:
+            fn()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)] for _ in range(steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(steps):
+        ev[s][0].record(stream)
+        for q, (_, fn) in enumerate(phases):
+            fn()
+            ev[s][q + 1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([total], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total = float(tt.item())
+    per = {name: statistics.mean(e[q].elapsed_time(e[q + 1]) for e in ev) for q, (name, _) in enumerate(phases)}
+    return total / steps, per, clk
+
+
+def _init_dist():
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def _line(args, w_name, value, ms, dtype, config, phases, roof, cpu, e2e, launches, clk, err, world, **extra):
+    d = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded; no dataset)", "config": config,
+         "phases_ms": {k_: round(v_, 4) for k_, v_ in phases.items()}, "roofline": roof,
+         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "error": err}
+    d.update(extra)
+    return d
+
+
+def _hbm_roof(peaks, peak_kind, bytes_, ms, kernel):
+    ach = bytes_ / (ms * 1e-3) / 1e9
+    pk = peaks.get("hbm_gbs")
+    return {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk, "traffic": None,
+            "kernel": kernel, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)",
+            "algorithmic_per_launch": {"bytes": bytes_}}
+
+
+def run_hessian(args):
+    """H = A D A^T (Sec. 5.2's normal matrix): left sketch with col_scale = sqrt(D),
+    then the symmetric masked product (B~ = A~), BF16 operands."""
+    import torch
+    import oracle
+    from paper_1811_02653_gb300 import build, ops
+    from paper_1811_02653_gb300 import workloads as W
+    world, rank, _ = _init_dist()
+    build.build()
+    peaks, peak_kind = _peaks()
+    w = W.HESSIAN
+    offs, idx, val = w.left_sparse(range(w.m))
+    A = torch.zeros((w.m, w.n), dtype=torch.float32, device="cuda")
+    rows_of = torch.repeat_interleave(torch.arange(w.m, device="cuda"), torch.from_numpy(np.diff(offs)).cuda())
+    A[rows_of, torch.from_numpy(idx).cuda()] = torch.from_numpy(val).cuda()
+    del rows_of, idx, val
+    cs_h = w.col_scale()
+    cs = torch.from_numpy(cs_h).cuda()
+    p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
+    ws = torch.empty(ops.sketch_workspace(p, w.m), dtype=torch.uint8, device="cuda")
+    At, _ = ops.sketch_left(p, A, "bf16", col_scale=cs, workspace=ws, block_mask=w.mask)
+    H = torch.empty((w.m, w.m), dtype=torch.float32, device="cuda")
+    phases = [("sketch_left (pack + gather, col_scale)",
+               lambda: ops.sketch_left(p, A, "bf16", col_scale=cs, out=At, workspace=ws, block_mask=w.mask)),
+              ("gemm_masked (symmetric: B~ = A~)", lambda: ops.gemm_masked(p, At, At, w.mask, C=H))]
+    ms, per, clk = _time_phases(phases, args.steps, args.warmup, world)
+    flop_eff = 2.0 * w.m * w.n * w.m
+    value = world * flop_eff / (ms * 1e-3) / 1e12
+    t_sk = per[phases[0][0]]
+    sk_bytes = w.m * w.n * 4 + w.n * 4 + w.m * w.k * w.b * 2
+    roof = _hbm_roof(peaks, peak_kind, sk_bytes, t_sk, "pack_cols_kernel + sketch_gather_kernel (left sketch)")
+    gemm_flop = 2.0 * w.m * w.k * w.b * w.m
+    t_g = per[phases[1][0]]
+    gemm = {"tflops": gemm_flop / (t_g * 1e-3) / 1e12,
+            "frac_of_sustained_bf16": gemm_flop / (t_g * 1e-3) / 1e12 / peaks.get("bf16_tflops_sustained", 1710.4)}
+    err, cpu = None, None
+    if rank == 0 and not args.no_check:
+        rows = [0, 1, 777, 2048, 3333, 4095]
+        A_r = A[rows].cpu().numpy().astype(np.float64)
+        h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+        At_r = oracle.sketch_left(A_r, h, s, w.b, cs_h.astype(np.float64))
+        H_or = oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(At_r).T, w.b, w.mask)
+        H_ex = (A_r * cs_h.astype(np.float64) ** 2) @ A_r.T
+        H_s = H[rows][:, rows].cpu().numpy().astype(np.float64)
+        err = {"vs_oracle_rel_frob": oracle.rel_frob(H_s, H_or), "vs_exact_rel_frob": oracle.rel_frob(H_s, H_ex),
+               "sample": f"{len(rows)}x{len(rows)} entries of H; oracle emulates bf16 operand rounding"}
+        if not args.no_cpu_baseline:
+            nr = 2
+            t0 = time.perf_counter()
+            At_c = oracle.sketch_left(A_r[:nr], h, s, w.b, cs_h.astype(np.float64))
+            oracle.masked_product(At_c, At_c.T, w.b, w.mask)
+            t_cpu = time.perf_counter() - t0
+            cpu = {"value": 2.0 * nr * w.n * nr / t_cpu / 1e12, "unit": UNIT,
+                   "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+                   "sample": f"{nr} rows of A at full n={w.n} with sqrt(D): sketch and the {nr}x{nr} block of H in FP64"}
+    cfg = {"workload": w.name, "m": w.m, "n": w.n, "l": w.m, "b": w.b, "N": w.N, "e": w.e,
+           "kept_blocks": [j for j in range(w.P) if (w.mask >> j) & 1], "gemm_dtype": "bf16",
+           "input_dtype": "f32", "l2": "inputs (17.2 GB) larger than L2; no flush needed",
+           "parallelism": f"replicas{world}"}
+    line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, cpu,
+                 None, 3 * args.steps, clk, err, world, gemm=gemm)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args):
+    """256 uneven products in one CUDA graph (parallel sketch branches, one
+    grouped persistent tcgen05 GEMM), autotuned."""
+    import torch
+    import oracle
+    from paper_1811_02653_gb300 import build, ops
+    from paper_1811_02653_gb300 import workloads as W
+    world, rank, _ = _init_dist()
+    build.build()
+    peaks, peak_kind = _peaks()
+    shapes = W.batched_shapes()
+    dev = []
+    for q, (m, n, l) in enumerate(shapes):
+        A, B = W.batched_device_inputs(shapes, q, "cuda")
+        C = torch.empty((m, l), dtype=torch.float32, device="cuda")
+        dev.append((A, B, C, ops.plan(n, n // 32, 4, 1, 0), 0b11111 & ~(1 << (q % 5))))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch = ops.Batch(dev, tune=not args.no_tune)
+    t_create = time.perf_counter() - t0
+    info = batch.info()
+    ms, per, clk = _time_phases([("graph (sketches + grouped GEMM)", batch.run)], args.steps, args.warmup, world)
+    flop_eff = float(sum(2 * m * n * l for m, n, l in shapes))
+    value = world * flop_eff / (ms * 1e-3) / 1e12
+    sk_bytes = sum((m + l) * n * 4 + (m + l) * 4 * (n // 32) * 2 for m, n, l in shapes)
+    roof = _hbm_roof(peaks, peak_kind, sk_bytes, ms,
+                     "whole graph (pack_cols, sketch_gather, gemm_grouped): sketch bytes / run time")
+    gemm_flop = float(sum(2 * m * 4 * (n // 32) * l for m, n, l in shapes))
+    err = None
+    if rank == 0 and not args.no_check:
+        sample = [0, 100, 255, max(range(256), key=lambda q: shapes[q][1])]
+        worst = 0.0
+        for q in sample:
+            A, B, C, p, mask = dev[q]
+            m, n, l = shapes[q]
+            rows, cols = sorted({0, m // 2, m - 1}), sorted({0, l // 3, l - 1})
+            A_r = A[rows].cpu().numpy().astype(np.float64)
+            B_c = B[:, cols].cpu().numpy().astype(np.float64)
+            h, s = oracle.hash_tables(n, n // 32, 4, 1, 0)
+            ref = oracle.masked_product(oracle.round_bf16(oracle.sketch_left(A_r, h, s, n // 32)),
+                                        oracle.round_bf16(oracle.sketch_right(B_c, h, s, n // 32)), n // 32, mask)
+            worst = max(worst, oracle.rel_frob(C[rows][:, cols].cpu().numpy().astype(np.float64), ref))
+        err = {"vs_oracle_rel_frob_max": worst,
+               "sample": f"3x3 entries of C in products {sample}; oracle emulates bf16 operand rounding"}
+    cfg = {"workload": "batched: 256 uneven products, m,l ~ U[256,4096], n log-U[8192,131072], b=n/32, N=4, e=1, "
+                       "product p drops block p mod 5", "count": 256,
+           "input_bytes": sum((m + l) * n * 4 for m, n, l in shapes), "gemm_dtype": "bf16", "input_dtype": "f32",
+           "l2": "inputs (182 GB) larger than L2; no flush needed", "parallelism": f"replicas{world}",
+           "graph": {k_: v_ for k_, v_ in info.items()}, "create_s": round(t_create, 2)}
+    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, None, None,
+                 info["kernel_launches"] * args.steps, clk, err, world,
+                 gemm={"flop_per_run": gemm_flop})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
+def run_autograd(args):
+    """Forward C = (X S)(S^T G)/k and backward dX, dG through the autograd Function."""
+    import torch
+    import oracle
+    from paper_1811_02653_gb300 import build, ops
+    from paper_1811_02653_gb300 import autograd as AG
+    from paper_1811_02653_gb300 import workloads as W
+    world, rank, _ = _init_dist()
+    build.build()
+    peaks, peak_kind = _peaks()
+    w = W.AUTOGRAD
+    X = torch.from_numpy(w.left()).to(torch.bfloat16).cuda().requires_grad_(True)
+    G = torch.from_numpy(w.right_cols(range(w.l))).to(torch.bfloat16).cuda().t().contiguous().requires_grad_(True)
+    dC = torch.from_numpy(w.upstream_grad()).cuda()
+    p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
+    state = {}
+
+    def fwd():
+        state["C"] = AG.oversketch_matmul(X, G, p, w.mask, args.recompute)
+
+    def bwd():
+        X.grad = None
+        G.grad = None
+        state["C"].backward(dC)
+
+    ms, per, clk = _time_phases([("forward", fwd), ("backward", bwd)], args.steps, args.warmup, world)
+    flop_eff = 6.0 * w.m * w.n * w.l          # exact forward + the two exact gradient GEMMs
+    value = world * flop_eff / (ms * 1e-3) / 1e12
+    t_f = per["forward"]
+    fwd_bytes = (w.m * w.n + w.n * w.l) * 2 + (w.m + w.l) * w.k * w.b * 2 + w.m * w.l * 4
+    roof = _hbm_roof(peaks, peak_kind, fwd_bytes, t_f, "forward: left + right sketch + masked GEMM")
+    err = None
+    if rank == 0 and not args.no_check:
+        rows, cols = [0, 2048, 4095], [0, 1024, 4095]
+        h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+        X_r = X.detach()[rows].float().cpu().numpy().astype(np.float64)
+        G_c = G.detach()[:, cols].float().cpu().numpy().astype(np.float64)
+        ref = oracle.masked_product(oracle.round_bf16(oracle.sketch_left(X_r, h, s, w.b)),
+                                    oracle.round_bf16(oracle.sketch_right(G_c, h, s, w.b)), w.b, w.mask)
+        err = {"forward_vs_oracle_rel_frob": oracle.rel_frob(
+            state["C"].detach()[rows][:, cols].cpu().numpy().astype(np.float64), ref),
+            "sample": "3x3 entries of C (gradients: tests/test_gpu_autograd.py)"}
+    cfg = {"workload": w.name, "m": w.m, "n": w.n, "l": w.l, "b": w.b, "N": w.N, "e": w.e,
+           "kept_blocks": [j for j in range(w.P) if (w.mask >> j) & 1], "gemm_dtype": "bf16",
+           "input_dtype": "bf16", "recompute": bool(args.recompute),
+           "metric_note": "effective flop = 6mnl (forward + dX + dG as exact GEMMs)",
+           "l2": "inputs (1.07 GB) larger than L2; no flush needed", "parallelism": f"replicas{world}"}
+    line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, None, None, None, clk, err, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,9 +685,19 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-GEMM comparison")
+    ap.add_argument("--workload", default="square", choices=["square", "hessian", "batched", "autograd"],
+                    help="square (default: the headline line), or another workload of the suite")
+    ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
+    ap.add_argument("--recompute", action="store_true", help="autograd: recompute the sketches in backward")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "hessian":
+        return run_hessian(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "autograd":
+        return run_autograd(args)
     return run_ours(args)
 
 

@@ -129,15 +129,39 @@ class Workload:
             return _map_rows(lambda r: self._sparse_row(r), rows, self.n)
         return gaussian_rows(self.data_seed, _S_LEFT, rows, self.n, self.std)
 
-    def _sparse_row(self, r: int) -> np.ndarray:
-        """i.i.d. Bernoulli(density) support (count ~ Binomial, positions a
-        uniform subset) with N(0, std^2) values."""
+    def _sparse_entries(self, r: int):
+        """Row r of a sparse left operand as (sorted column indices, FP64
+        values): i.i.d. Bernoulli(density) support (count ~ Binomial,
+        positions a uniform subset) with N(0, std^2) values."""
         g = _rng(self.data_seed, _S_LEFT, r)
-        out = np.zeros(self.n, dtype=np.float64)
         cnt = int(g.binomial(self.n, self.density))
         idx = np.sort(g.choice(self.n, size=cnt, replace=False))
-        out[idx] = g.standard_normal(cnt) * self.std
+        return idx, g.standard_normal(cnt) * self.std
+
+    def _sparse_row(self, r: int) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.float64)
+        idx, val = self._sparse_entries(r)
+        out[idx] = val
         return out
+
+    def left_sparse(self, rows):
+        """Rows of a sparse left operand in CSR form (offsets int64, column
+        indices int64, values FP32 rounded once), the same entries as
+        ``left_rows``: lets a caller scatter the dense matrix on a device
+        without forming it on the host."""
+        rows = list(rows)
+        parts = [None] * len(rows)
+
+        def work(t):
+            parts[t] = self._sparse_entries(rows[t])
+
+        with ThreadPoolExecutor(_threads()) as ex:
+            list(ex.map(work, range(len(rows))))
+        offs = np.zeros(len(rows) + 1, dtype=np.int64)
+        offs[1:] = np.cumsum([len(ix) for ix, _ in parts])
+        idx = np.concatenate([ix for ix, _ in parts]).astype(np.int64)
+        val = np.concatenate([v for _, v in parts]).astype(np.float32)
+        return offs, idx, val
 
     # ---- right operand (n x l): column c from stream (data_seed, RIGHT, c) ----
     def right_cols(self, cols) -> np.ndarray:
@@ -213,6 +237,24 @@ def batched_shapes(count: int = 256, seed: int = 1004):
     n = np.exp(g.uniform(math.log(8192), math.log(131072), size=count))
     n = np.clip(np.round(n / 2048) * 2048, 8192, 131072).astype(np.int64)
     return [(int(a), int(c), int(d)) for a, c, d in zip(m, n, l)]
+
+
+def batched_device_inputs(shapes, p: int, device, seed: int = 1004, dtype=None):
+    """Inputs of product p of the uneven batch drawn on a CUDA device:
+    A_p (m x n) and B_p (n x l) row-major, i.i.d. N(0,1) FP32 from torch's
+    seeded Philox generator (one generator per product, seed
+    ``seed * 100003 + p``).  At the batch's full size (182 GB of inputs) the
+    host cannot draw them; the oracle reads sampled rows and columns of these
+    same tensors back from the device."""
+    import torch
+    m, n, l = shapes[p]
+    g = torch.Generator(device=device)
+    g.manual_seed(seed * 100003 + p)
+    A = torch.randn((m, n), generator=g, device=device, dtype=torch.float32)
+    B = torch.randn((n, l), generator=g, device=device, dtype=torch.float32)
+    if dtype is not None:
+        A, B = A.to(dtype), B.to(dtype)
+    return A, B
 
 
 def scaled(w: Workload, **kw) -> Workload:
