@@ -84,6 +84,8 @@ SKETCH_CASES = [
     (129, 4096, 257, 1024, 2, 1),      # one bucket per CTA tile row
     (64, 3000, 300, 128, 3, 1),        # right sketch: 128-wide strips in place + packed remainder
     (32, 2048, 384, 256, 2, 1),        # right sketch: whole 128-wide strips only
+    (130, 100_000, 70, 512, 3, 1),     # 4 windows of the sketched dimension, the last one ragged
+    (64, 70_001, 200, 4096, 2, 1),     # 3 windows with few members per (window, bucket) list
 ]
 
 
@@ -152,7 +154,8 @@ def test_sketch_bf16_input(ops):
 
 
 @pytest.mark.parametrize("m,n,l,b,N,e", [(256, 4096, 384, 256, 4, 1), (100, 5000, 33, 128, 3, 1),
-                                         (130, 3000, 301, 128, 2, 1)])   # in-place strips + packed remainder
+                                         (130, 3000, 301, 128, 2, 1),    # in-place strips + packed remainder
+                                         (96, 80_000, 260, 512, 2, 1)])  # several windows
 def test_sketch_fp8_parity(ops, m, n, l, b, N, e):
     rng = np.random.default_rng(13)
     A = (rng.standard_normal((m, n)) * np.exp(rng.standard_normal((m, 1)) * 3)).astype(np.float32)
