@@ -32,6 +32,7 @@ GEMM_CASES = [
     (1, 1, 64, 1, 0, 0b1),                 # single element
     (1000, 130, 1024, 2, 1, 0b110),        # K = 2048, l < tile width
     (640, 1536, 512, 8, 2, 0b1110111101),  # many tiles (persistent loop, both TMEM buffers)
+    (2100, 3000, 256, 4, 1, 0b11101),      # more tile pairs than clusters, the last pair half empty
 ]
 
 
@@ -131,7 +132,8 @@ def _split_tf32(x):
 
 
 @pytest.mark.parametrize("m,l,b,N,e,mask", [(128, 128, 32, 2, 1, 0b011), (300, 700, 128, 3, 2, 0b10101),
-                                            (1000, 130, 1024, 2, 1, 0b110), (1, 1, 64, 1, 0, 0b1)])
+                                            (1000, 130, 1024, 2, 1, 0b110), (1, 1, 64, 1, 0, 0b1),
+                                            (2100, 1000, 128, 3, 1, 0b1011)])
 def test_gemm_tf32x3_parity(ops, m, l, b, N, e, mask):
     # FP32 operands as hi/lo TF32 planes: three tensor-core products give FP32 accuracy
     rng = np.random.default_rng(m + 7 * l)
@@ -196,6 +198,7 @@ FP8_CASES = [
     (1000, 130, 1024, 2, 1, 0b110),        # K = 2048, l < tile width
     (129, 449, 128, 4, 1, 0b11110),        # l just past two tile widths
     (640, 1536, 512, 8, 2, 0b1110111101),  # many tiles (persistent loop, both accumulators)
+    (2100, 3000, 256, 4, 1, 0b11101),      # more tile pairs than clusters, the last pair half empty
 ]
 
 
