@@ -515,18 +515,29 @@ def run_hessian(args):
     cs_h = w.col_scale()
     cs = torch.from_numpy(cs_h).cuda()
     p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
-    ws = torch.empty(ops.sketch_workspace(p, w.m), dtype=torch.uint8, device="cuda")
-    At, _ = ops.sketch_left(p, A, "bf16", col_scale=cs, workspace=ws, block_mask=w.mask)
+    if args.dense_sketch:
+        ws = torch.empty(ops.sketch_workspace(p, w.m), dtype=torch.uint8, device="cuda")
+        At, _ = ops.sketch_left(p, A, "bf16", col_scale=cs, workspace=ws, block_mask=w.mask)
+        sk_name, sk_kernel = "sketch_left (pack + gather, col_scale)", "pack_cols_kernel + sketch_gather_kernel"
+
+        def sketch():
+            ops.sketch_left(p, A, "bf16", col_scale=cs, out=At, workspace=ws, block_mask=w.mask)
+    else:
+        # A is 1% dense: route only its nonzeros (Sec. 4's O(nnz) sketch), one CTA per row
+        At, _ = ops.sketch_left_sparse(p, A, "bf16", col_scale=cs, block_mask=w.mask)
+        sk_name, sk_kernel = "sketch_left_sparse (col_scale)", "sketch_left_sparse_kernel"
+
+        def sketch():
+            ops.sketch_left_sparse(p, A, "bf16", col_scale=cs, out=At, block_mask=w.mask)
     H = torch.empty((w.m, w.m), dtype=torch.float32, device="cuda")
-    phases = [("sketch_left (pack + gather, col_scale)",
-               lambda: ops.sketch_left(p, A, "bf16", col_scale=cs, out=At, workspace=ws, block_mask=w.mask)),
+    phases = [(sk_name, sketch),
               ("gemm_masked (symmetric: B~ = A~)", lambda: ops.gemm_masked(p, At, At, w.mask, C=H))]
     ms, per, clk = _time_phases(phases, args.steps, args.warmup, world)
     flop_eff = 2.0 * w.m * w.n * w.m
     value = world * flop_eff / (ms * 1e-3) / 1e12
     t_sk = per[phases[0][0]]
     sk_bytes = w.m * w.n * 4 + w.n * 4 + w.m * w.k * w.b * 2
-    roof = _hbm_roof(peaks, peak_kind, sk_bytes, t_sk, "pack_cols_kernel + sketch_gather_kernel (left sketch)")
+    roof = _hbm_roof(peaks, peak_kind, sk_bytes, t_sk, f"{sk_kernel} (left sketch)")
     gemm_flop = 2.0 * w.m * w.k * w.b * w.m
     t_g = per[phases[1][0]]
     gemm = {"tflops": gemm_flop / (t_g * 1e-3) / 1e12,
@@ -554,9 +565,9 @@ def run_hessian(args):
     cfg = {"workload": w.name, "m": w.m, "n": w.n, "l": w.m, "b": w.b, "N": w.N, "e": w.e,
            "kept_blocks": [j for j in range(w.P) if (w.mask >> j) & 1], "gemm_dtype": "bf16",
            "input_dtype": "f32", "l2": "inputs (17.2 GB) larger than L2; no flush needed",
-           "parallelism": f"replicas{world}"}
+           "sketch": "dense gather" if args.dense_sketch else "sparse rows", "parallelism": f"replicas{world}"}
     line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, cpu,
-                 None, 3 * args.steps, clk, err, world, gemm=gemm)
+                 None, (3 if args.dense_sketch else 2) * args.steps, clk, err, world, gemm=gemm)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -689,6 +700,7 @@ def main():
                     help="square (default: the headline line), or another workload of the suite")
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
     ap.add_argument("--recompute", action="store_true", help="autograd: recompute the sketches in backward")
+    ap.add_argument("--dense-sketch", action="store_true", help="hessian: sketch A with the dense gather path")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

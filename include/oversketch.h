@@ -169,6 +169,27 @@ OS_API os_status oversketch_sketch_right(oversketch_plan_t plan, const void *B, 
                                   size_t ws_bytes, void *stream);
 
 /* -------------------------------------------------------------------------
+ * Left sketch of a sparse operand stored dense (Alg. 4 step 3 over the
+ * nonzeros only; Sec. 4 prices sketching at O(nnz(A)(N+e))), e.g. the
+ * 1%-dense constraint matrix of the interior-point Hessian A D A^T (Sec. 5.2).
+ *   At[r, j*b + c] = sum_{i : A[r,i] != 0, h_j(i) = c} sigma_j(i) * s_i * A[r, i]
+ * The same operation, layouts, FP8 scale rule, block_mask semantics and
+ * errors as oversketch_sketch_left, without a workspace: one CTA per row
+ * reads the row once and keeps all k*b sums of the listed blocks on chip.
+ * Per bucket the FP32 sum runs over the nonzero members in ascending i; a
+ * term is s_i * A[r,i] rounded once, then added (exact zeros are skipped,
+ * which changes no sum).  Correct for any density, fast for sparse rows.
+ *   Limit: with k listed blocks, k*b <= 32768 and the row's k*b FP32 sums,
+ *   two tables of b bucket offsets and a buffer of 1024 entries fit in one
+ *   CTA's shared memory (4*k*b + 8*b + 20*1024 bytes <= about 226 KB), else
+ *   OS_ERR_UNSUPPORTED.
+ */
+OS_API os_status oversketch_sketch_left_sparse(oversketch_plan_t plan, const void *A, os_dtype a_t,
+                                        int64_t m, int64_t lda, void *At, os_dtype out_t,
+                                        int64_t ldat, float *scales, const float *col_scale,
+                                        uint64_t block_mask, void *stream);
+
+/* -------------------------------------------------------------------------
  * Left sketch without allocation.  The paper has no counterpart: this is a
  * library convenience.  Same operation, arguments and errors as
  * oversketch_sketch_left, but the packing workspace is a fixed scratch array
@@ -223,8 +244,13 @@ typedef struct {
     os_dtype gemm_dtype;      /* OS_F32, OS_BF16 or OS_FP8E4M3               */
     const float *col_scale;   /* device, length n, or NULL (A diag(s) S)     */
     int32_t symmetric;        /* 1: B is ignored and C = (1/k) A~_sel A~_sel^T */
-    int32_t reserved;
+    int32_t flags;            /* OS_OPT_* bits, 0 by default                  */
 } os_opts;
+
+/* os_opts.flags: A is sparse (stored dense): sketch it with
+ * oversketch_sketch_left_sparse when the kept blocks fit its limit (the
+ * dense path otherwise).  The result differs only in FP32 summation order. */
+#define OS_OPT_SPARSE_A 1
 
 OS_API os_status oversketch_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
                                     os_dtype a_t, os_dtype b_t, const os_opts *opts, size_t *bytes);

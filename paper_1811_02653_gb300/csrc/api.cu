@@ -7,7 +7,7 @@
 
 namespace osk {
 
-// implemented in sketch.cu / gemm_simt.cu / gemm_tc.cu
+// implemented in sketch.cu / sketch_sparse.cu / gemm_simt.cu / gemm_tc.cu
 size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t);
 os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
@@ -16,6 +16,10 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
                             void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
                             void *ws, size_t ws_bytes, cudaStream_t st);
+bool sketch_left_sparse_fits(const Plan *p, uint64_t block_mask);
+os_status sketch_left_sparse_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda, void *At,
+                                  os_dtype out_t, int64_t ldat, float *scales, const float *col_scale,
+                                  uint64_t block_mask, cudaStream_t st);
 os_status gemm_masked_f32(const Plan *p, const float *At, int64_t ldat, const float *BtT,
                           int64_t ldbt, int64_t m, int64_t l, uint64_t mask, float alpha, float beta,
                           float *C, int64_t ldc, cudaStream_t st);
@@ -223,7 +227,10 @@ extern "C" os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os
     const float *cs = opts ? opts->col_scale : nullptr;
     // Only the kept blocks are sketched: the dropped blocks' columns of A~ and
     // B~ would never be read by the masked GEMM.
-    OSK_TRY(sketch_left_impl(p, A, a_t, m, lda, At, g, L.ldat, as, cs, mask, lws, L.left_ws, st));
+    if (opts && (opts->flags & OS_OPT_SPARSE_A) && sketch_left_sparse_fits(p, mask))
+        OSK_TRY(sketch_left_sparse_impl(p, A, a_t, m, lda, At, g, L.ldat, as, cs, mask, st));
+    else
+        OSK_TRY(sketch_left_impl(p, A, a_t, m, lda, At, g, L.ldat, as, cs, mask, lws, L.left_ws, st));
     if (!sym) OSK_TRY(sketch_right_impl(p, B, b_t, l, ldb, BtT, g, L.ldbt, bs, mask, lws, L.left_ws, st));
     int k = 0;
     for (int j = 0; j < p->P; ++j) k += (int)((mask >> j) & 1ull);

@@ -29,6 +29,7 @@ struct Plan {
     uint32_t *pperm;
     uint32_t *poffs;
     int64_t pstride;
+    int32_t hashed;   // 1: hs is the seeded hash below (oversketch_plan); 0: tables given by the caller
     int device;
 };
 
@@ -57,6 +58,43 @@ inline size_t dtype_size(os_dtype t) {   // bytes per element of one plane
 struct Tf32Pair {
     float v;
 };
+
+#ifdef __CUDACC__
+// The plan's hash (Alg. 4 steps 1-2 made concrete): splitmix64's finaliser used
+// as a counter-based generator.  key_j = mix(seed + (j+1) gamma) per block,
+// w = mix(key_j + (i+1) gamma) per index, h_j(i) = ((w >> 32) * b) >> 32,
+// sigma_j(i) = -1 when w is odd.  Returned as h | sign << 31, the layout of hs.
+constexpr uint64_t kSplitmixGamma = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+__device__ __forceinline__ uint64_t block_key(uint64_t seed, int j) {
+    return splitmix_mix(seed + (uint64_t)(j + 1) * kSplitmixGamma);
+}
+
+__device__ __forceinline__ uint32_t hash_code(uint64_t key, int64_t i, int32_t b) {
+    const uint64_t w = splitmix_mix(key + (uint64_t)(i + 1) * kSplitmixGamma);
+    const uint32_t h = (uint32_t)(((w >> 32) * (uint64_t)(uint32_t)b) >> 32);
+    return h | ((w & 1ull) ? kSignBit : 0u);
+}
+
+// FP8 block scale of the sketch outputs: the smallest e with amax <= 448 * 2^e
+// (exact), clamped to the UE8M0 range; 0 for an all-zero slice.
+__device__ __forceinline__ int fp8_scale_exponent(float amax) {
+    if (!(amax > 0.f)) return 0;
+    int E;
+    const float m = frexpf(amax, &E);   // amax = m * 2^E, m in [0.5, 1)
+    int e = (m <= 0.875f) ? E - 9 : E - 8;
+    return e < -127 ? -127 : (e > 127 ? 127 : e);
+}
+#endif
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 

@@ -24,27 +24,13 @@ namespace osk {
 
 namespace {
 
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
-
-__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
-    z ^= z >> 30;
-    z *= 0xBF58476D1CE4E5B9ull;
-    z ^= z >> 27;
-    z *= 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return z;
-}
-
 __global__ void plan_hash_kernel(int64_t n, int32_t b, uint64_t seed, uint32_t *__restrict__ hs) {
     const int j = blockIdx.y;
-    const uint64_t key = splitmix_mix(seed + (uint64_t)(j + 1) * kGamma);
+    const uint64_t key = block_key(seed, j);
     uint32_t *row = hs + (int64_t)j * n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t w = splitmix_mix(key + (uint64_t)(i + 1) * kGamma);
-        const uint32_t h = (uint32_t)(((w >> 32) * (uint64_t)(uint32_t)b) >> 32);
-        row[i] = h | ((w & 1ull) ? kSignBit : 0u);
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+        row[i] = hash_code(key, i, b);
 }
 
 // cnt[(j*nchunks + ch)*b + c] = #{i in chunk ch : h_j(i) = c}
@@ -211,6 +197,7 @@ os_status alloc_plan(int64_t n, int32_t b, int32_t N, int32_t e, uint64_t seed, 
     p->e = e;
     p->P = N + e;
     p->seed = seed;
+    p->hashed = 0;
     p->hs = p->perm = p->offs = p->pperm = p->poffs = nullptr;
     p->pstride = (n + 3 * (int64_t)b + 3) / 4 * 4;
     cudaGetDevice(&p->device);
@@ -243,6 +230,7 @@ extern "C" os_status oversketch_plan(int64_t n, int32_t b, int32_t N, int32_t e,
     plan_hash_kernel<<<dim3((unsigned)blocks_x, (unsigned)p->P), 256, 0, st>>>(n, b, seed, p->hs);
     os_status s = check_launch();
     if (s == OS_OK) s = build_csr(p, st);
+    p->hashed = 1;
     if (s != OS_OK) {
         free_plan(p);
         return s;

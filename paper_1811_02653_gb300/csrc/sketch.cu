@@ -75,15 +75,6 @@ struct Loader {
     __device__ __forceinline__ static float load1(const InT *p) { return to_f32(p[0]); }
 };
 
-// Smallest e with amax <= 448 * 2^e (exact), clamped to the UE8M0 range.
-__device__ __forceinline__ int fp8_scale_exponent(float amax) {
-    if (!(amax > 0.f)) return 0;
-    int E;
-    const float m = frexpf(amax, &E);   // amax = m * 2^E, m in [0.5, 1)
-    int e = (m <= 0.875f) ? E - 9 : E - 8;
-    return e < -127 ? -127 : (e > 127 ? 127 : e);
-}
-
 // Sixteen bytes of zeros: the row segment that padding entries of the bucket
 // lists point at, so the gather loop needs no predication.
 __device__ __align__(16) float g_zero_row[8];

@@ -38,7 +38,9 @@ class OverSketchError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("gemm_dtype", ctypes.c_int), ("col_scale", ctypes.c_void_p),
-                ("symmetric", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("symmetric", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+OPT_SPARSE_A = 1
 
 
 class _Problem(ctypes.Structure):
@@ -93,6 +95,7 @@ def load_library(path: str | None = None):
             "oversketch_gemm_bf16": (st, [vp, i64, vp, i64, i64, i64, i64, f32, f32, vp, i64, vp]),
             "oversketch_select_transpose": (st, [vp, st, i64, i64, i64, u64, i32, vp, st, i64, vp]),
             "oversketch_cast": (st, [vp, st, i64, i64, i64, vp, st, i64, vp]),
+            "oversketch_sketch_left_sparse": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, u64, vp]),
             "oversketch_batch_create": (st, [ctypes.POINTER(_Problem), i32, st, st, st, sz, i32, vp, pp]),
             "oversketch_batch_run": (st, [vp, vp]),
             "oversketch_batch_info": (st, [vp, ctypes.POINTER(_BatchInfo)]),
@@ -119,7 +122,7 @@ def _sigs_names():
             "oversketch_frob", "oversketch_device_status", "oversketch_sketch_left_noalloc",
             "oversketch_gemm_bf16", "oversketch_select_transpose", "oversketch_cast",
             "oversketch_batch_create", "oversketch_batch_run", "oversketch_batch_info",
-            "oversketch_batch_destroy"]
+            "oversketch_batch_destroy", "oversketch_sketch_left_sparse"]
 
 
 def _check(status: int, what: str):
@@ -287,6 +290,24 @@ def sketch_left(p: Plan, A: torch.Tensor, out_dtype="f32", col_scale=None, out=N
     return out, scales
 
 
+def sketch_left_sparse(p: Plan, A: torch.Tensor, out_dtype="f32", col_scale=None, out=None,
+                       scales=None, block_mask=0, stream=None):
+    """A~ = A diag(col_scale) S for a sparse A stored dense (only the nonzeros are
+    routed; no workspace); returns (At, scales or None)."""
+    lda = _rowmajor(A, "A")
+    m = A.shape[0]
+    od = _dtype_code(out_dtype)
+    ld = _pad_ld(p.z, od)
+    if out is None:
+        out = _alloc_out(m, ld, p.z, od, A.device)
+    if od == FP8 and scales is None:
+        scales = torch.empty(_fp8_scales_shape(m, p.z), dtype=torch.float32, device=A.device)
+    _check(load_library().oversketch_sketch_left_sparse(
+        p.handle, _ptr(A), _dt(A), m, lda, _ptr(out), od, out.stride(0), _ptr(scales),
+        _ptr(col_scale), block_mask, _stream(stream)), "oversketch_sketch_left_sparse")
+    return out, scales
+
+
 def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=None, block_mask=0,
                  workspace=None, stream=None):
     """B~^T = (S^T B)^T (l x z, K-major); returns (BtT, scales or None)."""
@@ -321,9 +342,9 @@ def gemm_masked(p: Plan, At, BtT, mask: int, alpha=None, beta=0.0, C=None, a_sca
     return C
 
 
-def _opts(gemm_dtype, col_scale=None, symmetric=False):
+def _opts(gemm_dtype, col_scale=None, symmetric=False, sparse_a=False):
     return _Opts(_dtype_code(gemm_dtype), col_scale.data_ptr() if col_scale is not None else None,
-                 1 if symmetric else 0, 0)
+                 1 if symmetric else 0, OPT_SPARSE_A if sparse_a else 0)
 
 
 def workspace_size(p: Plan, m: int, l: int, a_dtype=torch.float32, gemm_dtype="f32",
@@ -338,8 +359,9 @@ def workspace_size(p: Plan, m: int, l: int, a_dtype=torch.float32, gemm_dtype="f
 
 
 def matmul(p: Plan, A, B, mask: int, gemm_dtype="f32", col_scale=None, symmetric=False, C=None,
-           workspace=None, stream=None):
-    """The whole OverSketch product (A S)(S^T B)/k over the kept blocks."""
+           workspace=None, stream=None, sparse_a=False):
+    """The whole OverSketch product (A S)(S^T B)/k over the kept blocks.
+    ``sparse_a``: A is sparse (stored dense); its sketch routes only the nonzeros."""
     lda = _rowmajor(A, "A")
     m, n = A.shape
     if symmetric:
@@ -349,7 +371,7 @@ def matmul(p: Plan, A, B, mask: int, gemm_dtype="f32", col_scale=None, symmetric
         l, bt, bp = B.shape[1], _dt(B), _ptr(B)
     if C is None:
         C = torch.empty((m, l), dtype=torch.float32, device=A.device)
-    o = _opts(gemm_dtype, col_scale, symmetric)
+    o = _opts(gemm_dtype, col_scale, symmetric, sparse_a)
     if workspace is None:
         workspace = torch.empty(workspace_size(p, m, l, A.dtype, gemm_dtype, symmetric,
                                                B.dtype if B is not None else torch.float32),

@@ -41,7 +41,10 @@ def test_hessian_workload_sampled(ops):
     del rows_of
     cs = w.col_scale()
     p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
-    H = ops.matmul(p, A, None, w.mask, "bf16", col_scale=torch.from_numpy(cs).cuda(), symmetric=True)
+    csd = torch.from_numpy(cs).cuda()
+    # the sparse-row sketch (what the bench times) and the dense gather path
+    H = ops.matmul(p, A, None, w.mask, "bf16", col_scale=csd, symmetric=True, sparse_a=True)
+    H_dense = ops.matmul(p, A, None, w.mask, "bf16", col_scale=csd, symmetric=True)
     torch.cuda.synchronize()
     assert ops.device_status() == 0
     rows = [0, 1, 777, 2048, 3333, 4095]
@@ -56,6 +59,7 @@ def test_hessian_workload_sampled(ops):
     H_ref = oracle.masked_product(At, At.T, w.b, w.mask)
     H_gpu = H[rows][:, rows].cpu().numpy().astype(np.float64)
     assert oracle.rel_frob(H_gpu, H_ref) <= 1e-4
+    assert oracle.rel_frob(H_dense[rows][:, rows].cpu().numpy().astype(np.float64), H_ref) <= 1e-4
     # symmetric by construction (B~ = A~)
     assert np.array_equal(H_gpu, H_gpu.T)
     # the sketched H against the exact A D A^T on the sample (reported by the bench, loose here)
