@@ -86,6 +86,7 @@ SKETCH_CASES = [
     (32, 2048, 384, 256, 2, 1),        # right sketch: whole 128-wide strips only
     (130, 100_000, 70, 512, 3, 1),     # 4 windows of the sketched dimension, the last one ragged
     (64, 70_001, 200, 4096, 2, 1),     # 3 windows with few members per (window, bucket) list
+    (64, 20_000, 1023, 512, 3, 1),     # right operand rows not 16-byte aligned: 4-byte loads in place
 ]
 
 
