@@ -485,6 +485,220 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
     }
 }
 
+// ---------------------------------------------------------------------------
+// BF16 masked GEMM on CTA pairs (cta_group::2).  A pair of CTAs on two SMs
+// computes a 256 x 256 tile: CTA r stages rows 128r .. 128r+127 of the tile's A
+// panel and rows 128r .. 128r+127 of its B panel; the even CTA (the leader)
+// issues one 256 x 256 x 16 MMA per K slice that reads both CTAs' shared memory
+// and accumulates into both CTAs' TMEM (each holds its 128 rows x 256 columns).
+// A K step thus writes and reads 32 KB of each SM's shared memory per 512
+// tensor clocks instead of 48 KB, which is what bounds the one-CTA kernel.
+//   warp 0      TMA producer of this CTA's half (completion on the leader's barrier)
+//   warp 1      TMEM (both CTAs, jointly); MMA issue and commits (leader)
+//   warps 2..5  epilogue of this CTA's 128 rows; release the accumulator on the leader
+// Waits are bounded as in gemm_masked_tc_kernel.
+struct CfgPair {
+    static constexpr int BN = 256;                    // tile columns (the pair's N)
+    static constexpr int STAGES = 6;
+    static constexpr int BKE = ROWB / 2;              // 64 BF16 per K step
+    static constexpr int A_BYTES = BM * ROWB;         // this CTA's 128 rows of A
+    static constexpr int B_BYTES = (BN / 2) * ROWB;   // this CTA's 128 rows of B
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t PAIR_TX = 2u * STAGE_BYTES;   // both CTAs' loads land on the leader's barrier
+    static constexpr int TMEM_COLS = 512;             // two 256-column accumulators
+    static constexpr int THREADS = 192;
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+    static constexpr uint32_t IDESC = idesc_bf16_f32(2 * BM, BN);
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+__global__ void __launch_bounds__(CfgPair::THREADS, 1)
+gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
+                      const GemmArgs g) {
+    using C = CfgPair;
+    constexpr int STAGES = C::STAGES, BN = C::BN, BKE = C::BKE;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *tiles = smem;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_BYTES);   // leader's are used
+    uint64_t *empty = full + STAGES;
+    uint64_t *tmem_full = empty + STAGES;
+    uint64_t *tmem_empty = tmem_full + 2;                                          // leader's are used
+    uint64_t *drain = tmem_empty + 2;
+    uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_base_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = (int)cluster_ctarank();
+    const bool leader = rank == 0;
+    const int t_first = blockIdx.x / 2, t_step = gridDim.x / 2;
+    const int tiles_mp = (g.tiles_m + 1) / 2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tmem_full[a], 1);
+            mbar_init(&tmem_empty[a], 2 * 128);   // the epilogue threads of both CTAs
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_barrier_init();
+        prefetch_tmap(&tmap_a);
+        prefetch_tmap(&tmap_b);
+    }
+    if (warp == 1) tmem_alloc_pair(tmem_base_slot, C::TMEM_COLS);
+    tc_fence_before();
+    cluster_sync_all();   // both CTAs' barriers exist before any remote arrival
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_base_slot;
+
+    auto coords = [&](int t, int &tm, int &tn) {
+        int pm = 0;
+        tile_coords(t, tiles_mp, g.tiles_n, pm, tn);
+        tm = 2 * pm + rank;   // past the last tile (odd count): zero rows, no stores
+    };
+
+    if (warp == 0) {
+        // ---------------- TMA producer (this CTA's half of every stage) ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_phase[STAGES];
+            bool issued[STAGES];
+            for (int s = 0; s < STAGES; ++s) issued[s] = false, issued_phase[s] = 0;
+            bool ok = true;
+            for (int t = t_first; ok && t < g.num_tiles; t += t_step) {
+                int tm, tn;
+                coords(t, tm, tn);
+                for (int kb = 0; kb < g.num_kb; ++kb) {
+                    if (!mbar_wait_cluster(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
+                    const int blk = kb / g.kb_per_blk;
+                    const int kz = g.kept.idx[blk] * g.b + (kb - blk * g.kb_per_blk) * BKE;
+                    uint8_t *st = tiles + stage * C::STAGE_BYTES;
+                    const uint32_t fb = cluster_addr(&full[stage], 0);
+                    if (leader) mbar_expect_tx(&full[stage], C::PAIR_TX);
+                    tma_load_2d_pair(&tmap_a, fb, st, kz, tm * BM);
+                    tma_load_2d_pair(&tmap_b, fb, st + C::A_BYTES, kz, tn * BN + rank * (BN / 2));
+                    issued[stage] = true;
+                    issued_phase[stage] = phase;
+                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                }
+            }
+            // every stage this CTA loaded has been consumed by the pair's MMAs (so its
+            // copies have landed and no commit is still on its way here)
+            for (int s = 0; ok && s < STAGES; ++s)
+                if (issued[s] && !mbar_wait_cluster(&empty[s], issued_phase[s], abort)) ok = false;
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (leader; lane 0 issues, the warp waits together) ----------------
+        if (leader) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int iter = 0;
+            bool ok = true;
+            bool any = false;
+            for (int t = t_first; ok && t < g.num_tiles; t += t_step, ++iter) {
+                const int a = iter & 1;
+                const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+                if (!__all_sync(0xffffffffu, mbar_wait_cluster(&tmem_empty[a], aphase ^ 1u, abort))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(a * BN);
+                for (int kb = 0; kb < g.num_kb; ++kb) {
+                    if (!__all_sync(0xffffffffu, mbar_wait_cluster(&full[stage], phase, abort))) { ok = false; break; }
+                    tc_fence_after();
+                    if (lane == 0) {
+                        const uint32_t sa0 = smem_u32(tiles + stage * C::STAGE_BYTES);
+                        const uint32_t sb0 = sa0 + C::A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < ROWB / 32; ++kk)
+                            umma_f16_pair(d, sdesc_kmajor_sw128(sa0 + kk * 32), sdesc_kmajor_sw128(sb0 + kk * 32),
+                                          C::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+                        umma_commit_pair(&empty[stage], 0x3);   // the stage is free in both CTAs
+                    }
+                    __syncwarp();
+                    any = true;
+                    if (++stage == STAGES) stage = 0, phase ^= 1u;
+                }
+                if (!ok) break;
+                if (lane == 0) umma_commit_pair(&tmem_full[a], 0x3);   // both halves of the accumulator
+            }
+            if (!ok && any && lane == 0) {
+                // drain: wait for the MMAs already issued before TMEM is freed
+                umma_commit_pair(drain, 0x1);
+                mbar_wait_drain(drain, 0);
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5): this CTA's 128 rows ----------------
+        const int quarter = warp & 3;
+        const int row_in_tile = quarter * 32 + lane;
+        const uint32_t empty_cl0 = cluster_addr(&tmem_empty[0], 0);
+        const uint32_t empty_cl1 = cluster_addr(&tmem_empty[1], 0);
+        int iter = 0;
+        for (int t = t_first; t < g.num_tiles; t += t_step, ++iter) {
+            int tm, tn;
+            coords(t, tm, tn);
+            const int a = iter & 1;
+            const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+            if (!__all_sync(0xffffffffu, mbar_wait_cluster(&tmem_full[a], aphase, abort))) break;
+            tc_fence_after();
+            const int64_t r = (int64_t)tm * BM + row_in_tile;
+            const int64_t c0 = (int64_t)tn * BN;
+            const bool vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15u) == 0) && (g.ldc % 4 == 0);
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN + ch * 32), v);
+                if (r < g.m) {
+                    float *dst = g.C + r * g.ldc + c0 + ch * 32;
+                    const int64_t cb = c0 + ch * 32;
+                    if (vec_ok && cb + 32 <= g.l) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            float4 o = make_float4(g.alpha * __uint_as_float(v[4 * u]),
+                                                   g.alpha * __uint_as_float(v[4 * u + 1]),
+                                                   g.alpha * __uint_as_float(v[4 * u + 2]),
+                                                   g.alpha * __uint_as_float(v[4 * u + 3]));
+                            if (g.beta != 0.f) {
+                                const float4 old = *reinterpret_cast<const float4 *>(dst + 4 * u);
+                                o.x = fmaf(g.beta, old.x, o.x);
+                                o.y = fmaf(g.beta, old.y, o.y);
+                                o.z = fmaf(g.beta, old.z, o.z);
+                                o.w = fmaf(g.beta, old.w, o.w);
+                            }
+                            *reinterpret_cast<float4 *>(dst + 4 * u) = o;
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) {
+                            if (cb + u < g.l) {
+                                float o = g.alpha * __uint_as_float(v[u]);
+                                if (g.beta != 0.f) o = fmaf(g.beta, dst[u], o);
+                                dst[u] = o;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive_cluster(a == 0 ? empty_cl0 : empty_cl1);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();   // both CTAs are done with the shared TMEM and with each other's barriers
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, C::TMEM_COLS);
+    }
+}
+
 // ---------------------------------------------------------------- host ----
 
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -597,9 +811,65 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
     return check_launch();
 }
 
+// BF16 on CTA pairs (gemm_pair_bf16_kernel): 256 x 256 tiles, two SMs each.
+os_status launch_pair_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l, int64_t zK,
+                           int32_t blk, const BlockList &kept, float alpha, float beta, float *Cout, int64_t ldc,
+                           cudaStream_t st) {
+    using C = CfgPair;
+    if (blk % C::BKE != 0) return OS_ERR_UNSUPPORTED;
+    if (!aligned16(A) || !aligned16(B) || (lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0) return OS_ERR_INVALID_ARG;
+    if (zK >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.m = m;
+    g.l = l;
+    g.b = blk;
+    g.kb_per_blk = blk / C::BKE;
+    g.kept = kept;
+    g.num_kb = kept.count * g.kb_per_blk;
+    g.tiles_m = (int)((m + BM - 1) / BM);
+    g.tiles_n = (int)((l + C::BN - 1) / C::BN);
+    g.num_tiles = (g.tiles_m + 1) / 2 * g.tiles_n;   // tile pairs
+    g.alpha = alpha;
+    g.beta = beta;
+    g.C = Cout;
+    g.ldc = ldc;
+    CUtensorMap ta, tb;
+    OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, zK, lda, BM, C::BKE));
+    OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, zK, ldb, C::BN / 2, C::BKE));
+    static bool attr_set = false;
+    if (!attr_set) {
+        OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_pair_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)C::SMEM));
+        attr_set = true;
+    }
+    const int pairs = num_sms() / 2;
+    const int grid = 2 * (g.num_tiles < pairs ? g.num_tiles : pairs);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    OSK_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_pair_bf16_kernel, ta, tb, g));
+    return check_launch();
+}
+
+#ifndef OSK_GEMM_PAIR
+#define OSK_GEMM_PAIR 1
+#endif
+
 os_status launch_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l, int64_t zK,
                       int32_t blk, const BlockList &kept, float alpha, float beta, float *C, int64_t ldc,
                       cudaStream_t st) {
+    if (OSK_GEMM_PAIR)
+        return launch_pair_bf16(A, lda, B, ldb, m, l, zK, blk, kept, alpha, beta, C, ldc, st);
     return launch_tc<CfgBf16>(A, nullptr, lda, B, nullptr, ldb, m, l, zK, blk, kept, alpha, beta, C, ldc, st);
 }
 
