@@ -110,6 +110,36 @@ def _dist():
     return world, rank, local
 
 
+def _backend() -> str:
+    """NCCL between GPUs; gloo where no GPU is present (the CPU tests of this logic)."""
+    import torch
+    return "nccl" if torch.cuda.is_available() else "gloo"
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    """The largest of every rank's x (the step time the whole job waits for)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if _backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _job_value(flop_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job throughput in TFLOP/s: every rank runs its own product (weak
+    scaling), so the job does world x the per-rank work in the slowest rank's time."""
+    return world * flop_per_rank / (ms_max * 1e-3) / 1e12
+
+
 # ----------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ----------------------------------------------------------------------------
@@ -205,13 +235,7 @@ def run_ours(args):
     from paper_1811_02653_gb300 import build, ops
     from paper_1811_02653_gb300 import workloads as W
 
-    world, rank, local = _dist()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    world, rank, local = _init_dist()
     build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     w = _workload(args)
@@ -253,8 +277,7 @@ def run_ours(args):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
@@ -270,20 +293,15 @@ def run_ours(args):
         e[3].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = _max_over_ranks(t_start.elapsed_time(t_end), world)
     ms = total_ms / args.steps
     t_left = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     t_right = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
     t_gemm = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
     flop_eff = 2.0 * w.m * w.n * w.l
-    value = world * flop_eff / (ms * 1e-3) / 1e12
+    value = _job_value(flop_eff, ms, world)
 
     # ---- end to end through the C ABI with host buffers ----
     C_h = torch.empty((w.m, w.l), dtype=torch.float32).pin_memory()
@@ -304,7 +322,7 @@ def run_ours(args):
         e2e_step()
     s1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = s0.elapsed_time(s1) / e2e_steps
+    e2e_ms = _max_over_ranks(s0.elapsed_time(s1) / e2e_steps, world)
     h2d = A_h.numel() * 4 + B_h.numel() * 4
     d2h = C_h.numel() * 4
 
@@ -419,7 +437,7 @@ def run_ours(args):
             "config": _config(w, args),
             "phases_ms": {k_: round(v_, 4) for k_, v_ in phases.items()},
             "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": world * flop_eff / (e2e_ms * 1e-3) / 1e12, "unit": UNIT,
+            "e2e": {"value": _job_value(flop_eff, e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": 4 * args.steps, "clocks": clk, "error": err, "exact_gemm": exact}
     if rank == 0:
@@ -447,8 +465,7 @@ def _time_phases(phases, steps, warmup, world):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -459,27 +476,23 @@ def _time_phases(phases, steps, warmup, world):
             ev[s][q + 1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    _barrier(world)
     clk = clocks.stop()
-    total = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([total], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total = float(tt.item())
+    total = _max_over_ranks(t0.elapsed_time(t1), world)
     per = {name: statistics.mean(e[q].elapsed_time(e[q + 1]) for e in ev) for q, (name, _) in enumerate(phases)}
     return total / steps, per, clk
 
 
 def _init_dist():
+    """One process per GPU (torchrun's RANK / LOCAL_RANK / WORLD_SIZE, rendezvous at
+    MASTER_ADDR); a single process needs no process group."""
     import torch
     world, rank, local = _dist()
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local if world > 1 else 0)
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+        dist.init_process_group(_backend())
     return world, rank, local
 
 
@@ -539,7 +552,7 @@ def run_hessian(args):
               ("gemm_masked (symmetric: B~ = A~)", lambda: ops.gemm_masked(p, At, At, w.mask, C=H))]
     ms, per, clk = _time_phases(phases, args.steps, args.warmup, world)
     flop_eff = 2.0 * w.m * w.n * w.m
-    value = world * flop_eff / (ms * 1e-3) / 1e12
+    value = _job_value(flop_eff, ms, world)
     t_sk = per[phases[0][0]]
     sk_bytes = w.m * w.n * 4 + w.n * 4 + w.m * w.k * w.b * 2
     roof = _hbm_roof(peaks, peak_kind, sk_bytes, t_sk, f"{sk_kernel} (left sketch)")
@@ -601,7 +614,7 @@ def run_batched(args):
     info = batch.info()
     ms, per, clk = _time_phases([("graph (sketches + grouped GEMM)", batch.run)], args.steps, args.warmup, world)
     flop_eff = float(sum(2 * m * n * l for m, n, l in shapes))
-    value = world * flop_eff / (ms * 1e-3) / 1e12
+    value = _job_value(flop_eff, ms, world)
     sk_bytes = sum((m + l) * n * 4 + (m + l) * 4 * (n // 32) * 2 for m, n, l in shapes)
     roof = _hbm_roof(peaks, peak_kind, sk_bytes, ms,
                      "whole graph (pack_cols, sketch_gather, gemm_grouped): sketch bytes / run time")
@@ -663,7 +676,7 @@ def run_autograd(args):
 
     ms, per, clk = _time_phases([("forward", fwd), ("backward", bwd)], args.steps, args.warmup, world)
     flop_eff = 6.0 * w.m * w.n * w.l          # exact forward + the two exact gradient GEMMs
-    value = world * flop_eff / (ms * 1e-3) / 1e12
+    value = _job_value(flop_eff, ms, world)
     t_f = per["forward"]
     fwd_bytes = (w.m * w.n + w.n * w.l) * 2 + (w.m + w.l) * w.k * w.b * 2 + w.m * w.l * 4
     roof = _hbm_roof(peaks, peak_kind, fwd_bytes, t_f, "forward: left + right sketch + masked GEMM")
