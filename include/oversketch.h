@@ -259,6 +259,26 @@ OS_API os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os_dty
                             int64_t m, int64_t n, int64_t l, uint64_t mask, const os_opts *opts,
                             void *workspace, size_t ws_bytes, void *stream);
 
+/* The same product with A, B and C in HOST memory (page-locked memory lets the
+ * transfers overlap the kernels; pageable memory works, slower).  B is copied
+ * first and sketched while A arrives in chunks of rows, each chunk sketched as
+ * it lands; the masked GEMM runs in row panels and each panel of C is copied
+ * back while the next one is computed (BF16 products; FP8 and FP32 products
+ * sketch A and compute C in one piece).  The copies run on an internal stream of
+ * the device, ordered after the caller's earlier work on `stream`; the call is
+ * complete on `stream` once C is written (stream-ordered: synchronise `stream`
+ * before reading C).  workspace: device memory of
+ * oversketch_matmul_host_workspace_size bytes (the device copies of A, B and C
+ * and the sketched operands).  Same arguments and errors as oversketch_matmul,
+ * with the pointers A, B (ignored when symmetric) and C in host memory. */
+OS_API os_status oversketch_matmul_host_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
+                                                os_dtype a_t, os_dtype b_t, const os_opts *opts,
+                                                size_t *bytes);
+OS_API os_status oversketch_matmul_host(oversketch_plan_t plan, const void *A, os_dtype a_t, int64_t lda,
+                                 const void *B, os_dtype b_t, int64_t ldb, float *C, int64_t ldc,
+                                 int64_t m, int64_t n, int64_t l, uint64_t mask, const os_opts *opts,
+                                 void *workspace, size_t ws_bytes, void *stream);
+
 /* -------------------------------------------------------------------------
  * Adjoints of the sketch restricted to the kept blocks (the backward pass of
  * (*) as a function of A and B; S_sel is S of Eq. 3 restricted to the kept

@@ -2,6 +2,7 @@
 // whole-product entry point and the FP64 error reductions.
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
@@ -250,4 +251,206 @@ extern "C" os_status oversketch_frob(const float *X, int64_t ldx, const float *Y
     OSK_TRY(check_launch());
     frob_final_kernel<<<1, 32, 0, st>>>(part, kFrobBlocks, out);
     return check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// The whole product from and to HOST memory, with the transfers overlapped.
+//
+// Order on two streams (the caller's compute stream and an internal copy stream
+// of the device, ordered after the caller's earlier work):
+//   copy:    B (whole) | A chunk 0 | A chunk 1 | ...            | C panel 0 | C panel 1 ...
+//   compute:           | right sketch | left sketch chunk 0 | ... | GEMM panel 0 | panel 1 ...
+// The right sketch of B runs while A streams in; each chunk of A rows (a
+// multiple of 128 rows) is sketched as soon as it lands; the masked GEMM runs
+// in row panels and every panel of C goes back while the next one is computed.
+// The device copies use 16-byte aligned row pitches, so the right sketch always
+// gathers B in place.  FP8 and FP32 products (whose sketches carry scale rows or
+// TF32 planes sized by the full row count) sketch A in one piece.
+namespace osk {
+namespace {
+
+struct HostPlan {
+    int64_t lda_d, ldb_d, ldc_d;     // device row pitches (elements)
+    size_t a_bytes, b_bytes, c_bytes, mm_bytes;
+    int64_t a_rows, c_rows;           // rows per A chunk / per C panel
+};
+
+int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+HostPlan host_plan(const Plan *p, int64_t m, int64_t l, os_dtype a_t, os_dtype b_t, const os_opts *o) {
+    HostPlan h;
+    const bool sym = o && o->symmetric;
+    const size_t ea = dtype_size(a_t), eb = dtype_size(b_t);
+    h.lda_d = round_up(p->n, (int64_t)(16 / ea));
+    h.ldb_d = round_up(l, (int64_t)(16 / eb));
+    h.ldc_d = round_up(l, 4);
+    h.a_bytes = align256((size_t)m * h.lda_d * ea);
+    h.b_bytes = sym ? 0 : align256((size_t)p->n * h.ldb_d * eb);
+    h.c_bytes = align256((size_t)m * h.ldc_d * 4);
+    const os_dtype g = sketch_dtype(p, o ? o->gemm_dtype : OS_F32);
+    const bool chunked = g == OS_BF16;
+    h.a_rows = chunked ? (m + 7) / 8 : m;
+    h.a_rows = round_up(h.a_rows < 1 ? 1 : h.a_rows, 128);
+    h.c_rows = chunked ? round_up((m + 3) / 4, 128) : m;
+    if (h.c_rows < 1) h.c_rows = 1;
+    // oversketch_matmul's sketched operands, with the packing buffer sized for one
+    // A chunk and for the right sketch's ragged remainder (B is gathered in place)
+    const MatmulLayout L = layout(p, m, l, a_t, b_t, o);
+    const size_t wl = sketch_workspace_bytes(p, h.a_rows < m ? h.a_rows : m, a_t);
+    const size_t wr = sym ? 0 : sketch_workspace_bytes(p, b_t == OS_F32 ? 128 : l, b_t);
+    h.mm_bytes = L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes + align256(wl > wr ? wl : wr) + 256;
+    return h;
+}
+
+// 2-D copy that degenerates to one contiguous copy when the rows are packed.
+cudaError_t copy2d(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t height,
+                   cudaMemcpyKind kind, cudaStream_t st) {
+    if (dpitch == width && spitch == width) return cudaMemcpyAsync(dst, src, width * height, kind, st);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, st);
+}
+
+cudaStream_t copy_stream(int dev) {
+    static cudaStream_t streams[64] = {nullptr};
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
+}  // namespace
+}  // namespace osk
+
+extern "C" os_status oversketch_matmul_host_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
+                                                           os_dtype a_t, os_dtype b_t, const os_opts *opts,
+                                                           size_t *bytes) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p || !bytes || m < 0 || l < 0) return OS_ERR_INVALID_ARG;
+    if ((a_t != OS_F32 && a_t != OS_BF16) || (b_t != OS_F32 && b_t != OS_BF16)) return OS_ERR_DTYPE;
+    if (opts && opts->symmetric) l = m;
+    const HostPlan h = host_plan(p, m, l, a_t, b_t, opts);
+    *bytes = h.a_bytes + h.b_bytes + h.c_bytes + h.mm_bytes + 256;
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_matmul_host(oversketch_plan_t plan, const void *A, os_dtype a_t, int64_t lda,
+                                            const void *B, os_dtype b_t, int64_t ldb, float *C, int64_t ldc,
+                                            int64_t m, int64_t n, int64_t l, uint64_t mask, const os_opts *opts,
+                                            void *workspace, size_t ws_bytes, void *stream) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p || !A || !C) return OS_ERR_INVALID_ARG;
+    const bool sym = opts && opts->symmetric;
+    if (sym) l = m;
+    if (!sym && !B) return OS_ERR_INVALID_ARG;
+    if (n != p->n || m < 0 || l < 0 || lda < n || ldc < l || (!sym && ldb < l)) return OS_ERR_INVALID_ARG;
+    if ((a_t != OS_F32 && a_t != OS_BF16) || (!sym && b_t != OS_F32 && b_t != OS_BF16)) return OS_ERR_DTYPE;
+    if (sym) b_t = a_t;
+    OSK_TRY(check_mask(mask, p->P));
+    const os_dtype g0 = opts ? opts->gemm_dtype : OS_F32;
+    if (g0 != OS_F32 && g0 != OS_BF16 && g0 != OS_FP8E4M3) return OS_ERR_DTYPE;
+    const os_dtype g = sketch_dtype(p, g0);
+    const HostPlan h = host_plan(p, m, l, a_t, b_t, opts);
+    if (!workspace || ws_bytes < h.a_bytes + h.b_bytes + h.c_bytes + h.mm_bytes + 256) return OS_ERR_WORKSPACE;
+    if (m == 0 || l == 0) return OS_OK;
+    int dev = 0;
+    OSK_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device) return OS_ERR_INVALID_ARG;
+    cudaStream_t cs = as_stream(stream);
+    cudaStream_t xs = copy_stream(dev);
+    if (!xs) return OS_ERR_CUDA;
+    const size_t ea = dtype_size(a_t), eb = dtype_size(b_t);
+    char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
+    char *Ad = base;
+    char *Bd = base + h.a_bytes;
+    float *Cd = reinterpret_cast<float *>(base + h.a_bytes + h.b_bytes);
+    char *mm = base + h.a_bytes + h.b_bytes + h.c_bytes;
+    const MatmulLayout L = layout(p, m, l, a_t, b_t, opts);
+    void *At = mm;
+    void *BtT = sym ? At : mm + L.at_bytes;
+    float *as = g == OS_FP8E4M3 ? reinterpret_cast<float *>(mm + L.at_bytes + L.bt_bytes) : nullptr;
+    float *bs = g == OS_FP8E4M3 ? (sym ? as : reinterpret_cast<float *>(mm + L.at_bytes + L.bt_bytes + L.as_bytes))
+                                : nullptr;
+    void *pack = mm + L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes;
+    const size_t pack_bytes = h.mm_bytes - 256 - (L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes);
+    const float *cs_scale = opts ? opts->col_scale : nullptr;
+    const bool sparse = opts && (opts->flags & OS_OPT_SPARSE_A) && sketch_left_sparse_fits(p, mask);
+    const int64_t nchunks = (m + h.a_rows - 1) / h.a_rows;
+    const int64_t npanels = (m + h.c_rows - 1) / h.c_rows;
+
+    std::vector<cudaEvent_t> ev;
+    auto event = [&](cudaEvent_t *e) -> os_status {
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return set_cuda_error(cudaGetLastError());
+        ev.push_back(*e);
+        return OS_OK;
+    };
+    os_status st = OS_OK;
+    do {
+        // the copy stream starts after the caller's earlier work on `stream`
+        cudaEvent_t e0;
+        if ((st = event(&e0)) != OS_OK) break;
+        if (cudaEventRecord(e0, cs) != cudaSuccess || cudaStreamWaitEvent(xs, e0, 0) != cudaSuccess) {
+            st = set_cuda_error(cudaGetLastError());
+            break;
+        }
+        // B, then the right sketch while A arrives
+        if (!sym) {
+            cudaEvent_t eb_done;
+            if ((st = event(&eb_done)) != OS_OK) break;
+            if (copy2d(Bd, h.ldb_d * eb, B, ldb * eb, l * eb, n, cudaMemcpyHostToDevice, xs) != cudaSuccess ||
+                cudaEventRecord(eb_done, xs) != cudaSuccess || cudaStreamWaitEvent(cs, eb_done, 0) != cudaSuccess) {
+                st = set_cuda_error(cudaGetLastError());
+                break;
+            }
+            if ((st = sketch_right_impl(p, Bd, b_t, l, h.ldb_d, BtT, g, L.ldbt, bs, mask, pack, pack_bytes, cs)) != OS_OK)
+                break;
+        }
+        // A in chunks of rows, each sketched as it lands
+        for (int64_t c = 0; st == OS_OK && c < nchunks; ++c) {
+            const int64_t r0 = c * h.a_rows, rows = (m - r0 < h.a_rows) ? m - r0 : h.a_rows;
+            cudaEvent_t ea_done;
+            if ((st = event(&ea_done)) != OS_OK) break;
+            if (copy2d(Ad + (size_t)r0 * h.lda_d * ea, h.lda_d * ea, (const char *)A + (size_t)r0 * lda * ea, lda * ea,
+                       n * ea, rows, cudaMemcpyHostToDevice, xs) != cudaSuccess ||
+                cudaEventRecord(ea_done, xs) != cudaSuccess || cudaStreamWaitEvent(cs, ea_done, 0) != cudaSuccess) {
+                st = set_cuda_error(cudaGetLastError());
+                break;
+            }
+            void *at_c = (char *)At + (size_t)r0 * L.ldat * dtype_size(g);
+            const void *a_c = Ad + (size_t)r0 * h.lda_d * ea;
+            if (sparse)
+                st = sketch_left_sparse_impl(p, a_c, a_t, rows, h.lda_d, at_c, g, L.ldat, as, cs_scale, mask, cs);
+            else
+                st = sketch_left_impl(p, a_c, a_t, rows, h.lda_d, at_c, g, L.ldat, as, cs_scale, mask, pack, pack_bytes,
+                                      cs);
+        }
+        if (st != OS_OK) break;
+        // the GEMM in row panels; each panel of C goes back while the next is computed
+        int k = 0;
+        for (int j = 0; j < p->P; ++j) k += (int)((mask >> j) & 1ull);
+        for (int64_t q = 0; q < npanels; ++q) {
+            const int64_t r0 = q * h.c_rows, rows = (m - r0 < h.c_rows) ? m - r0 : h.c_rows;
+            const void *at_q = (const char *)At + (size_t)r0 * L.ldat * dtype_size(g);
+            const float *as_q = as ? as + r0 : nullptr;   // slice-major scales: the panel's rows start at r0
+            if ((st = oversketch_gemm_masked(plan, at_q, L.ldat, as_q, BtT, L.ldbt, bs, g, rows, l, mask,
+                                             1.0f / (float)k, 0.0f, Cd + r0 * h.ldc_d, h.ldc_d, cs)) != OS_OK)
+                break;
+            cudaEvent_t ec;
+            if ((st = event(&ec)) != OS_OK) break;
+            if (cudaEventRecord(ec, cs) != cudaSuccess || cudaStreamWaitEvent(xs, ec, 0) != cudaSuccess ||
+                copy2d(C + r0 * ldc, ldc * 4, Cd + r0 * h.ldc_d, h.ldc_d * 4, l * 4, rows, cudaMemcpyDeviceToHost,
+                       xs) != cudaSuccess) {
+                st = set_cuda_error(cudaGetLastError());
+                break;
+            }
+        }
+        if (st != OS_OK) break;
+        // the call is complete on `stream` once the last panel is in C
+        cudaEvent_t e_end;
+        if ((st = event(&e_end)) != OS_OK) break;
+        if (cudaEventRecord(e_end, xs) != cudaSuccess || cudaStreamWaitEvent(cs, e_end, 0) != cudaSuccess)
+            st = set_cuda_error(cudaGetLastError());
+    } while (0);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);   // released once their work completes
+    return st;
 }

@@ -96,6 +96,10 @@ def load_library(path: str | None = None):
             "oversketch_select_transpose": (st, [vp, st, i64, i64, i64, u64, i32, vp, st, i64, vp]),
             "oversketch_cast": (st, [vp, st, i64, i64, i64, vp, st, i64, vp]),
             "oversketch_sketch_left_sparse": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, u64, vp]),
+            "oversketch_matmul_host_workspace_size": (st, [vp, i64, i64, st, st, ctypes.POINTER(_Opts),
+                                                           ctypes.POINTER(sz)]),
+            "oversketch_matmul_host": (st, [vp, vp, st, i64, vp, st, i64, vp, i64, i64, i64, i64, u64,
+                                            ctypes.POINTER(_Opts), vp, sz, vp]),
             "oversketch_batch_create": (st, [ctypes.POINTER(_Problem), i32, st, st, st, sz, i32, vp, pp]),
             "oversketch_batch_run": (st, [vp, vp]),
             "oversketch_batch_info": (st, [vp, ctypes.POINTER(_BatchInfo)]),
@@ -122,7 +126,8 @@ def _sigs_names():
             "oversketch_frob", "oversketch_device_status", "oversketch_sketch_left_noalloc",
             "oversketch_gemm_bf16", "oversketch_select_transpose", "oversketch_cast",
             "oversketch_batch_create", "oversketch_batch_run", "oversketch_batch_info",
-            "oversketch_batch_destroy", "oversketch_sketch_left_sparse"]
+            "oversketch_batch_destroy", "oversketch_sketch_left_sparse",
+            "oversketch_matmul_host_workspace_size", "oversketch_matmul_host"]
 
 
 def _check(status: int, what: str):
@@ -155,6 +160,14 @@ def _dtype_code(d) -> int:
     if isinstance(d, torch.dtype):
         return _DT[d]
     return int(d)
+
+
+def _rowmajor_host(t: torch.Tensor, name: str):
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise OverSketchError(f"{name} must be a row-major 2-D tensor")
+    if t.is_cuda:
+        raise OverSketchError(f"{name} must live in host memory")
+    return t.stride(0)
 
 
 def _rowmajor(t: torch.Tensor, name: str):
@@ -379,6 +392,42 @@ def matmul(p: Plan, A, B, mask: int, gemm_dtype="f32", col_scale=None, symmetric
     _check(load_library().oversketch_matmul(
         p.handle, _ptr(A), _dt(A), lda, bp, bt, ldb, _ptr(C), C.stride(0), m, n, l, mask,
         ctypes.byref(o), _ptr(workspace), workspace.numel(), _stream(stream)), "oversketch_matmul")
+    return C
+
+
+def matmul_host_workspace(p: Plan, m: int, l: int, a_dtype=torch.float32, b_dtype=torch.float32,
+                          gemm_dtype="f32", symmetric=False, sparse_a=False) -> int:
+    out = ctypes.c_size_t()
+    o = _opts(gemm_dtype, None, symmetric, sparse_a)
+    _check(load_library().oversketch_matmul_host_workspace_size(
+        p.handle, m, l, _dtype_code(a_dtype), _dtype_code(b_dtype), ctypes.byref(o), ctypes.byref(out)),
+        "oversketch_matmul_host_workspace_size")
+    return out.value
+
+
+def matmul_host(p: Plan, A, B, mask: int, gemm_dtype="f32", C=None, col_scale=None, symmetric=False,
+                sparse_a=False, workspace=None, stream=None):
+    """(A S)(S^T B)/k with A, B and C in host memory (CPU tensors, ideally pinned):
+    the transfers overlap the kernels (oversketch_matmul_host).  Returns C on the
+    host; it is complete once `stream` is synchronised."""
+    lda = _rowmajor_host(A, "A")
+    m, n = A.shape
+    if symmetric:
+        l, ldb, bt, bp = m, 0, _dt(A), None
+    else:
+        ldb = _rowmajor_host(B, "B")
+        l, bt, bp = B.shape[1], _dt(B), _ptr(B)
+    if C is None:
+        C = torch.empty((m, l), dtype=torch.float32).pin_memory()
+    _rowmajor_host(C, "C")
+    o = _opts(gemm_dtype, col_scale, symmetric, sparse_a)
+    if workspace is None:
+        workspace = torch.empty(matmul_host_workspace(p, m, l, A.dtype, B.dtype if B is not None else A.dtype,
+                                                      gemm_dtype, symmetric, sparse_a),
+                                dtype=torch.uint8, device="cuda")
+    _check(load_library().oversketch_matmul_host(
+        p.handle, _ptr(A), _dt(A), lda, bp, bt, ldb, _ptr(C), C.stride(0), m, n, l, mask, ctypes.byref(o),
+        _ptr(workspace), workspace.numel(), _stream(stream)), "oversketch_matmul_host")
     return C
 
 
