@@ -20,11 +20,11 @@
 // translations of the random row accesses cheap; 128-byte pieces spread over
 // a 4 GB matrix ran at a quarter to a half of the L2 gather rate on GB300.
 //
-// A gather CTA owns 32 consecutive sketched columns q (whole buckets of one
-// block) and one strip.  Each warp walks the bucket-CSR of its buckets
+// A gather CTA owns 16 consecutive sketched columns q (32 for FP8 output;
+// whole buckets of one block) and one strip.  Each warp walks the bucket-CSR of its buckets
 // (indices ascending inside a bucket, the same order in every run: no
 // atomics, bitwise reproducible) and gathers row pieces with 16-byte loads,
-// accumulating in FP32.  The 32-column x 128-row tile is transposed through
+// accumulating in FP32.  The (16 or 32)-column x 128-row tile is transposed through
 // shared memory so that Y^T rows are written contiguously.  CTAs of one strip
 // are adjacent in launch order, so a strip stays in L2 while all of its
 // buckets are gathered.  For FP8 output the four CTAs that own the quarters of
@@ -101,7 +101,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
     constexpr int PITCH = TF + 1;        // odd pitch: conflict-free column reads
     constexpr int G = 2 * SLOTS;         // groups of 4 members per batch: 8 loads per lane in flight
     constexpr int QPW = QT / kWarps;     // buckets per warp
-    static_assert(QT == 32 || QT == 128, "tile of 32 or 128 sketched columns");
+    static_assert(QT == 8 || QT == 16 || QT == 32 || QT == 128, "tile of 8, 16, 32 or 128 sketched columns");
     static_assert(SLOTS == 1 || SLOTS == 2 || SLOTS == 4, "1, 2 or 4 members per warp load");
     extern __shared__ float4 smem_tile[];
     float *tile = reinterpret_cast<float *>(smem_tile);   // [QT][PITCH]
@@ -228,7 +228,32 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
         cl.sync();   // the partial maxima stay readable until every rank is done
     } else {
         // Transposed write-out: warp w writes rows f0 + 16w .. 16w+15 of Y^T.
-        constexpr int VPL = QT / 32;         // values per lane per row
+        if constexpr (QT < 32) {
+            // 32 / QT rows per warp pass, QT lanes per row
+            constexpr int RPI = 32 / QT;
+            const int qq = lane % QT, rr = lane / QT;
+            for (int t = 0; t < TF / kWarps; t += RPI) {
+                const int ff = warp * (TF / kWarps) + t + rr;
+                const int64_t frow = f0 + ff;
+                const int q = q0 + qq;
+                if (frow < F && q < qend) {
+                    const float v = tile[qq * PITCH + ff];
+                    OutT *dst = Yt + frow * ldy + q;
+                    if constexpr (std::is_same<OutT, Tf32Pair>::value) {
+                        float *d0 = reinterpret_cast<float *>(dst);
+                        const float hi = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+                        d0[0] = hi;
+                        d0[plane_elems] = v - hi;
+                    } else if constexpr (sizeof(OutT) == 4) {
+                        *dst = v;
+                    } else {
+                        *dst = __float2bfloat16_rn(v);
+                    }
+                }
+            }
+            return;
+        }
+        constexpr int VPL = QT >= 32 ? QT / 32 : 1;   // values per lane per row
         for (int t = 0; t < TF / kWarps; ++t) {
             const int ff = warp * (TF / kWarps) + t;
             const int64_t frow = f0 + ff;
@@ -430,6 +455,12 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
 
 // Gather from an operand packed in 128-wide strips (n rows each) in tiles of
 // 32 sketched columns, which keeps the CTAs that run together on few strips.
+// Sketched columns per gather CTA (FP8 outputs: 32, the quarter of a scale slice).
+// 16 puts 512 CTAs on each strip of the square workload (b = 1024, 8 kept
+// blocks), so fewer strips are in flight at once than with 32 and more of the
+// gathered rows hit L2 (right sketch 1.89 -> 1.74 ms on GB300).
+constexpr int kGatherQT = 16;
+
 template <typename InT>
 os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *col_scale, void *Yt,
                         os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask,
@@ -438,15 +469,15 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *co
     const int64_t ss = p->n * kStrip;
     switch (out_t) {
         case OS_F32:
-            return launch_gather_t<InT, float, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks, st);
+            return launch_gather_t<InT, float, kGatherQT, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks, st);
         case OS_BF16:
-            return launch_gather_t<InT, __nv_bfloat16, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<InT, __nv_bfloat16, kGatherQT, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
                                                               blocks, st);
         case OS_FP8E4M3:
             return launch_gather_t<InT, __nv_fp8_e4m3, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
                                                                blocks, st);
         case OS_TF32X2:
-            return launch_gather_t<InT, Tf32Pair, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks,
+            return launch_gather_t<InT, Tf32Pair, kGatherQT, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks,
                                                          st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
@@ -461,15 +492,15 @@ os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
     switch (out_t) {
         case OS_F32:
-            return launch_gather_t<float, float, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks, st);
+            return launch_gather_t<float, float, kGatherQT, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks, st);
         case OS_BF16:
-            return launch_gather_t<float, __nv_bfloat16, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld,
+            return launch_gather_t<float, __nv_bfloat16, kGatherQT, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld,
                                                                 blocks, st);
         case OS_FP8E4M3:
             return launch_gather_t<float, __nv_fp8_e4m3, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, scales, scale_ld,
                                                                  blocks, st);
         case OS_TF32X2:
-            return launch_gather_t<float, Tf32Pair, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks,
+            return launch_gather_t<float, Tf32Pair, kGatherQT, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks,
                                                            st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
