@@ -95,7 +95,7 @@ struct Cfg {
     }
 };
 
-using CfgBf16 = Cfg<256, 4, Kind::Bf16>;
+using CfgBf16 = Cfg<256, 4, Kind::Bf16>;        // grouped launches (single products run on CTA pairs)
 using CfgBf16N128 = Cfg<128, 6, Kind::Bf16>;   // narrower tiles for grouped launches of small products
 using CfgTf32x3 = Cfg<128, 3, Kind::Tf32x3>;
 using CfgFp8 = Cfg<224, 4, Kind::Fp8>;
@@ -861,16 +861,10 @@ os_status launch_pair_bf16(const void *A, int64_t lda, const void *B, int64_t ld
     return check_launch();
 }
 
-#ifndef OSK_GEMM_PAIR
-#define OSK_GEMM_PAIR 1
-#endif
-
 os_status launch_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l, int64_t zK,
                       int32_t blk, const BlockList &kept, float alpha, float beta, float *C, int64_t ldc,
                       cudaStream_t st) {
-    if (OSK_GEMM_PAIR)
-        return launch_pair_bf16(A, lda, B, ldb, m, l, zK, blk, kept, alpha, beta, C, ldc, st);
-    return launch_tc<CfgBf16>(A, nullptr, lda, B, nullptr, ldb, m, l, zK, blk, kept, alpha, beta, C, ldc, st);
+    return launch_pair_bf16(A, lda, B, ldb, m, l, zK, blk, kept, alpha, beta, C, ldc, st);
 }
 
 }  // namespace
