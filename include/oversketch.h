@@ -122,6 +122,18 @@ OS_API os_status oversketch_plan_info(oversketch_plan_t plan, int64_t *n, int32_
 /* Release the plan's device tables (synchronises the device first). */
 OS_API os_status oversketch_plan_destroy(oversketch_plan_t plan);
 
+/* Number of blocks for a target accuracy (Thm. 4.1).  d = 2/(eps*theta) sketch
+ * columns make the product (eps, theta)-accurate:
+ *   ||AB - (AS)(S^T B)||_F^2 <= eps ||A||_F^2 ||B||_F^2 with probability >= 1 - theta.
+ * With blocks of width b: *N = ceil(r*d/b) (r >= 1 multiplies the dimension, as
+ * the paper's remark after the theorem does for the spectral-norm bound), and *e
+ * = the smallest e with e >= p*(N + e) for a straggler fraction p in [0, 1): the
+ * N + e blocks still hold N after a fraction p of them is dropped.  Host-only.
+ * Errors: OS_ERR_INVALID_ARG (eps <= 0, theta outside (0,1), b < 1, r < 1, p
+ * outside [0,1)); OS_ERR_UNSUPPORTED when N + e would exceed 64. */
+OS_API os_status oversketch_sketch_size(double eps, double theta, int32_t b, double straggler_fraction,
+                                 int32_t r, int32_t *N, int32_t *e);
+
 /* -------------------------------------------------------------------------
  * Sketches (Alg. 5: A~ = A S block by block; B~ = S^T B).
  *

@@ -1,5 +1,6 @@
 // C ABI glue: status strings, mask handling, the masked-GEMM dispatcher, the
 // whole-product entry point and the FP64 error reductions.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -453,4 +454,28 @@ extern "C" os_status oversketch_matmul_host(oversketch_plan_t plan, const void *
     } while (0);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);   // released once their work completes
     return st;
+}
+
+// Sketch size for a target accuracy (Thm. 4.1): d = 2/(eps*theta) columns make
+// (A S)(S^T B) (eps, theta)-accurate, i.e. ||AB - A S S^T B||_F^2 <= eps ||A||_F^2 ||B||_F^2
+// with probability at least 1 - theta; with blocks of width b that is N = ceil(r d / b)
+// blocks (r >= 1 multiplies the dimension as in the spectral-norm remark after the
+// theorem), and e extra blocks absorb the stragglers: the smallest e with
+// e >= p (N + e) for a straggler fraction p, so that dropping a fraction p of the
+// N + e blocks still leaves N.  Host-only; no device is touched.
+extern "C" os_status oversketch_sketch_size(double eps, double theta, int32_t b, double straggler_fraction,
+                                            int32_t r, int32_t *N, int32_t *e) {
+    if (!N || !e || !(eps > 0.0) || !(theta > 0.0) || theta >= 1.0 || b < 1 || r < 1) return OS_ERR_INVALID_ARG;
+    if (!(straggler_fraction >= 0.0) || straggler_fraction >= 1.0) return OS_ERR_INVALID_ARG;
+    const double d = 2.0 / (eps * theta);
+    const double nb = std::ceil((double)r * d / (double)b - 1e-9);
+    if (nb > 64.0) return OS_ERR_UNSUPPORTED;
+    const int32_t n_blocks = nb < 1.0 ? 1 : (int32_t)nb;
+    const double p = straggler_fraction;
+    const double ex = std::ceil(p * (double)n_blocks / (1.0 - p) - 1e-9);
+    const int32_t extra = ex < 0.0 ? 0 : (int32_t)ex;
+    if (n_blocks + extra > 64) return OS_ERR_UNSUPPORTED;
+    *N = n_blocks;
+    *e = extra;
+    return OS_OK;
 }

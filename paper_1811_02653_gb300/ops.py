@@ -100,6 +100,8 @@ def load_library(path: str | None = None):
                                                            ctypes.POINTER(sz)]),
             "oversketch_matmul_host": (st, [vp, vp, st, i64, vp, st, i64, vp, i64, i64, i64, i64, u64,
                                             ctypes.POINTER(_Opts), vp, sz, vp]),
+            "oversketch_sketch_size": (st, [ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, i32,
+                                            ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "oversketch_batch_create": (st, [ctypes.POINTER(_Problem), i32, st, st, st, sz, i32, vp, pp]),
             "oversketch_batch_run": (st, [vp, vp]),
             "oversketch_batch_info": (st, [vp, ctypes.POINTER(_BatchInfo)]),
@@ -127,7 +129,7 @@ def _sigs_names():
             "oversketch_gemm_bf16", "oversketch_select_transpose", "oversketch_cast",
             "oversketch_batch_create", "oversketch_batch_run", "oversketch_batch_info",
             "oversketch_batch_destroy", "oversketch_sketch_left_sparse",
-            "oversketch_matmul_host_workspace_size", "oversketch_matmul_host"]
+            "oversketch_matmul_host_workspace_size", "oversketch_matmul_host", "oversketch_sketch_size"]
 
 
 def _check(status: int, what: str):
@@ -239,6 +241,15 @@ class Plan:
 
 def plan(n, b, N, e, seed=0, stream=None) -> Plan:
     return Plan(n, b, N, e, seed, stream)
+
+
+def sketch_size(eps: float, theta: float, b: int, straggler_fraction: float = 0.0, r: int = 1):
+    """(N, e) for an (eps, theta)-accurate product with blocks of width b (Thm. 4.1):
+    N = ceil(r * 2/(eps*theta) / b), e = smallest e >= p (N + e)."""
+    N, e = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().oversketch_sketch_size(eps, theta, b, straggler_fraction, r, ctypes.byref(N),
+                                                 ctypes.byref(e)), "oversketch_sketch_size")
+    return N.value, e.value
 
 
 def plan_from_tables(h, sigma, b, N, e, stream=None) -> Plan:
