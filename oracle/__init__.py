@@ -18,6 +18,8 @@ Every function cites the passage it follows:
                         Alg. 4 step 3), the implicit (hash-loop) form.
 * ``masked_product`` -- Alg. 3 computation + termination + reduction phases:
                         sum over the kept blocks j of A~_j B~_j, scaled 1/k.
+* ``masked_product_blocks`` -- the same with Alg. 3's termination rule applied
+                        to every block of C on its own (its own kept set).
 * ``gradients``      -- the adjoint of the bilinear map C(X, G) of Eq. 3.
 * ``expected_sq_error`` -- Lemma "countEV" (appendix B) exact variance, summed
                         over the entries of C as in Lemma "lemma2".
@@ -213,6 +215,31 @@ def masked_product(At, Bt, b: int, mask: int) -> np.ndarray:
     for j in sel:
         C += At[:, j * b:(j + 1) * b] @ Bt[j * b:(j + 1) * b, :]
     return C / len(sel)
+
+
+def masked_product_blocks(At, Bt, b: int, masks, bm: int, bn: int) -> np.ndarray:
+    """Alg. 3's termination rule applied to every block of C separately: block
+    (i, j) of C (rows i*bm .., columns j*bn ..) is the reduction of its own kept
+    sketch blocks, C(i, j) = (1/k_ij) sum_{t in masks[i][j]} A~(i, t) B~(t, j);
+    a block with no kept sketch block is zero.  masks[i][j] is a bit mask of the
+    kept blocks t (ascending)."""
+    At = np.asarray(At, dtype=np.float64)
+    Bt = np.asarray(Bt, dtype=np.float64)
+    P = At.shape[1] // b
+    assert At.shape[1] == P * b and Bt.shape[0] == P * b
+    m, l = At.shape[0], Bt.shape[1]
+    C = np.zeros((m, l), dtype=np.float64)
+    for i in range((m + bm - 1) // bm):
+        for j in range((l + bn - 1) // bn):
+            if int(masks[i][j]) == 0:
+                continue
+            sel = selected_blocks(int(masks[i][j]), P)
+            rs, cs = slice(i * bm, min(m, (i + 1) * bm)), slice(j * bn, min(l, (j + 1) * bn))
+            acc = np.zeros((rs.stop - rs.start, cs.stop - cs.start), dtype=np.float64)
+            for t in sel:
+                acc += At[rs, t * b:(t + 1) * b] @ Bt[t * b:(t + 1) * b, cs]
+            C[rs, cs] = acc / len(sel)
+    return C
 
 
 def oversketch(A, B, h, sigma, b: int, mask: int, col_scale=None) -> np.ndarray:

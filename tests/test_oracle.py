@@ -371,3 +371,42 @@ def test_fp8_scale_exponent():
     assert np.abs(q).max() <= 448
     deq = oracle.dequantize_fp8_rows(q, e)
     assert oracle.rel_frob(deq, x) < 0.05
+
+
+def test_masked_product_blocks_reduces_to_one_mask():
+    # the same kept set in every block of C is the single-mask product
+    rng = np.random.default_rng(41)
+    b, P = 8, 5
+    At = rng.standard_normal((21, P * b))
+    Bt = rng.standard_normal((P * b, 13))
+    mask = 0b10110
+    masks = [[mask] * 4 for _ in range(6)]                    # 4 x 4 blocks, ragged edges
+    C = oracle.masked_product_blocks(At, Bt, b, masks, 4, 4)
+    assert np.allclose(C, oracle.masked_product(At, Bt, b, mask), rtol=1e-13, atol=1e-13)
+
+
+def test_masked_product_blocks_brute_force():
+    # block (i, j) of C from the explicit sketch: A (S_ij S_ij^T / k_ij) B with S_ij the
+    # kept columns of Eq. 3's S; an empty kept set gives a zero block
+    rng = np.random.default_rng(42)
+    n, b, N, e = 40, 4, 3, 2
+    P = N + e
+    h, s = oracle.hash_tables(n, b, N, e, 3)
+    S = oracle.sketch_matrix(h, s, b)
+    A = rng.standard_normal((10, n))
+    B = rng.standard_normal((n, 7))
+    bm, bn = 4, 3
+    masks = [[int(rng.integers(1, 1 << P)) for _ in range(3)] for _ in range(3)]
+    masks[1][2] = 0
+    C = oracle.masked_product_blocks(A @ S, S.T @ B, b, masks, bm, bn)
+    for i in range(3):
+        for j in range(3):
+            rs, cs = slice(i * bm, min(10, (i + 1) * bm)), slice(j * bn, min(7, (j + 1) * bn))
+            if masks[i][j] == 0:
+                assert (C[rs, cs] == 0).all()
+                continue
+            cols = [t * b + q for t in range(P) if (masks[i][j] >> t) & 1 for q in range(b)]
+            Ssel = S[:, cols]
+            k = bin(masks[i][j]).count("1")
+            ref = A[rs] @ (Ssel @ Ssel.T / k) @ B[:, cs]
+            assert np.allclose(C[rs, cs], ref, rtol=1e-12, atol=1e-12)
