@@ -249,6 +249,20 @@ OS_API os_status oversketch_gemm_masked(oversketch_plan_t plan, const void *At, 
                                  uint64_t mask, float alpha, float beta, float *C, int64_t ldc,
                                  void *stream);
 
+/* Alg. 3's termination rule per block of C: the reduction of block (i, j)
+ * (rows i*bm .., columns j*bn ..) keeps its own set of sketch blocks,
+ *   C(i, j) = (1/k_ij) sum_{t in masks[i*nbc + j]} At(i, t) BtT(j, t)^T  (+ beta C(i, j)),
+ * nbc = ceil(l / bn), k_ij = popcount of the mask.  block_masks: DEVICE array of
+ * ceil(m/bm) * nbc masks (bits >= N+e are ignored; an empty mask gives a zero
+ * block).  At, BtT: BF16 sketches holding every block that any mask keeps.  bm and
+ * bn: multiples of 256 (the CTA-pair tile), e.g. the paper's b x b blocks.
+ * Errors: OS_ERR_INVALID_ARG, OS_ERR_UNSUPPORTED (bm or bn not a multiple of 256,
+ * b not a multiple of 64), OS_ERR_CUDA. */
+OS_API os_status oversketch_gemm_masked_blocks(oversketch_plan_t plan, const void *At, int64_t ldat,
+                                        const void *BtT, int64_t ldbt, int64_t m, int64_t l,
+                                        const uint64_t *block_masks, int64_t bm, int64_t bn,
+                                        float beta, float *C, int64_t ldc, void *stream);
+
 /* -------------------------------------------------------------------------
  * The whole product (*): left sketch, right sketch, masked GEMM.
  */

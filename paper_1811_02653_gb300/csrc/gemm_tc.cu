@@ -118,6 +118,11 @@ struct GemmArgs {
     float *C;
     int64_t ldc;
     BlockList kept;
+    // per-block masks (CTA-pair kernel): block (i, j) of C is bm x bn, its kept set
+    // block_masks[i * nbc + j] (bits >= P ignored); null: `kept` for every tile
+    const uint64_t *block_masks;
+    int64_t bm, bn;
+    int32_t nbc, P;
 };
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
@@ -560,6 +565,17 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
         tile_coords(t, tiles_mp, g.tiles_n, pm, tn);
         tm = 2 * pm + rank;   // past the last tile (odd count): zero rows, no stores
     };
+    // kept sketch blocks of the block of C holding tile pair (tm / 2, tn) (the pair's
+    // 256 rows and 256 columns lie in one block: bm and bn are multiples of 256)
+    const uint64_t pmask = g.P >= 64 ? ~0ull : ((1ull << g.P) - 1ull);
+    auto tile_mask = [&](int tm, int tn) -> uint64_t {
+        if (!g.block_masks) return 0ull;
+        const int64_t bi = (int64_t)(tm >> 1) * (2 * BM) / g.bm, bj = (int64_t)tn * BN / g.bn;
+        return __ldg(g.block_masks + bi * g.nbc + bj) & pmask;
+    };
+    auto tile_num_kb = [&](uint64_t msk) -> int {
+        return g.block_masks ? __popcll(msk) * g.kb_per_blk : g.num_kb;
+    };
 
     if (warp == 0) {
         // ---------------- TMA producer (this CTA's half of every stage) ----------------
@@ -573,10 +589,23 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
             for (int t = t_first; ok && t < g.num_tiles; t += t_step) {
                 int tm, tn;
                 coords(t, tm, tn);
-                for (int kb = 0; kb < g.num_kb; ++kb) {
+                const uint64_t msk = tile_mask(tm, tn);
+                const int nkb = tile_num_kb(msk);
+                uint64_t rest = msk;
+                int kidx = 0;
+                for (int kb = 0, kin = 0; kb < nkb; ++kb) {
                     if (!mbar_wait_cluster(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
-                    const int blk = kb / g.kb_per_blk;
-                    const int kz = g.kept.idx[blk] * g.b + (kb - blk * g.kb_per_blk) * BKE;
+                    if (kin == 0) {
+                        // the next kept sketch block of this tile
+                        if (g.block_masks) {
+                            kidx = __ffsll((long long)rest) - 1;
+                            rest &= rest - 1;
+                        } else {
+                            kidx = g.kept.idx[kb / g.kb_per_blk];
+                        }
+                    }
+                    const int kz = kidx * g.b + kin * BKE;
+                    if (++kin == g.kb_per_blk) kin = 0;
                     uint8_t *st = tiles + stage * C::STAGE_BYTES;
                     const uint32_t fb = cluster_addr(&full[stage], 0);
                     if (leader) mbar_expect_tx(&full[stage], C::PAIR_TX);
@@ -603,13 +632,16 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
             for (int t = t_first; ok && t < g.num_tiles; t += t_step, ++iter) {
                 const int a = iter & 1;
                 const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+                int tm, tn;
+                coords(t, tm, tn);
+                const int nkb = tile_num_kb(tile_mask(tm, tn));
                 if (!__all_sync(0xffffffffu, mbar_wait_cluster(&tmem_empty[a], aphase ^ 1u, abort))) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(a * BN);
-                for (int kb = 0; kb < g.num_kb; ++kb) {
+                for (int kb = 0; kb < nkb; ++kb) {
                     if (!__all_sync(0xffffffffu, mbar_wait_cluster(&full[stage], phase, abort))) { ok = false; break; }
                     tc_fence_after();
                     if (lane == 0) {
@@ -651,19 +683,27 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
             const int64_t r = (int64_t)tm * BM + row_in_tile;
             const int64_t c0 = (int64_t)tn * BN;
             const bool vec_ok = ((reinterpret_cast<uintptr_t>(g.C) & 15u) == 0) && (g.ldc % 4 == 0);
+            // per-block masks: 1/k of this tile's block; an empty kept set gives zeros
+            const uint64_t msk = tile_mask(tm, tn);
+            const bool none = g.block_masks && msk == 0;
+            const float alpha = g.block_masks ? (none ? 0.f : 1.f / (float)__popcll(msk)) : g.alpha;
             for (int ch = 0; ch < BN / 32; ++ch) {
                 uint32_t v[32];
                 tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * BN + ch * 32), v);
+                if (none) {
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) v[u] = 0u;
+                }
                 if (r < g.m) {
                     float *dst = g.C + r * g.ldc + c0 + ch * 32;
                     const int64_t cb = c0 + ch * 32;
                     if (vec_ok && cb + 32 <= g.l) {
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
-                            float4 o = make_float4(g.alpha * __uint_as_float(v[4 * u]),
-                                                   g.alpha * __uint_as_float(v[4 * u + 1]),
-                                                   g.alpha * __uint_as_float(v[4 * u + 2]),
-                                                   g.alpha * __uint_as_float(v[4 * u + 3]));
+                            float4 o = make_float4(alpha * __uint_as_float(v[4 * u]),
+                                                   alpha * __uint_as_float(v[4 * u + 1]),
+                                                   alpha * __uint_as_float(v[4 * u + 2]),
+                                                   alpha * __uint_as_float(v[4 * u + 3]));
                             if (g.beta != 0.f) {
                                 const float4 old = *reinterpret_cast<const float4 *>(dst + 4 * u);
                                 o.x = fmaf(g.beta, old.x, o.x);
@@ -677,7 +717,7 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
 #pragma unroll
                         for (int u = 0; u < 32; ++u) {
                             if (cb + u < g.l) {
-                                float o = g.alpha * __uint_as_float(v[u]);
+                                float o = alpha * __uint_as_float(v[u]);
                                 if (g.beta != 0.f) o = fmaf(g.beta, dst[u], o);
                                 dst[u] = o;
                             }
@@ -814,7 +854,8 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
 // BF16 on CTA pairs (gemm_pair_bf16_kernel): 256 x 256 tiles, two SMs each.
 os_status launch_pair_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l, int64_t zK,
                            int32_t blk, const BlockList &kept, float alpha, float beta, float *Cout, int64_t ldc,
-                           cudaStream_t st) {
+                           cudaStream_t st, const uint64_t *block_masks = nullptr, int64_t bm = 0,
+                           int64_t bn = 0, int32_t P = 0) {
     using C = CfgPair;
     if (blk % C::BKE != 0) return OS_ERR_UNSUPPORTED;
     if (!aligned16(A) || !aligned16(B) || (lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0) return OS_ERR_INVALID_ARG;
@@ -834,6 +875,11 @@ os_status launch_pair_bf16(const void *A, int64_t lda, const void *B, int64_t ld
     g.beta = beta;
     g.C = Cout;
     g.ldc = ldc;
+    g.block_masks = block_masks;
+    g.bm = bm;
+    g.bn = bn;
+    g.nbc = bn > 0 ? (int32_t)((l + bn - 1) / bn) : 0;
+    g.P = P;
     CUtensorMap ta, tb;
     OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, zK, lda, BM, C::BKE));
     OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, zK, ldb, C::BN / 2, C::BKE));
@@ -985,4 +1031,19 @@ extern "C" os_status oversketch_gemm_bf16(const void *A, int64_t lda, const void
     for (int t = 0; t < 64; ++t) one.idx[t] = 0;
     const int64_t kpad = (K + 63) / 64 * 64;
     return launch_bf16(A, lda, B, ldb, m, n, K, (int32_t)kpad, one, alpha, beta, C, ldc, as_stream(stream));
+}
+
+extern "C" os_status oversketch_gemm_masked_blocks(oversketch_plan_t plan, const void *At, int64_t ldat,
+                                                   const void *BtT, int64_t ldbt, int64_t m, int64_t l,
+                                                   const uint64_t *block_masks, int64_t bm, int64_t bn,
+                                                   float beta, float *C, int64_t ldc, void *stream) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p || !At || !BtT || !C || !block_masks || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
+    const int64_t z = (int64_t)p->P * p->b;
+    if (ldat < z || ldbt < z) return OS_ERR_INVALID_ARG;
+    if (bm < 256 || bn < 256 || bm % 256 != 0 || bn % 256 != 0) return OS_ERR_UNSUPPORTED;
+    if (m == 0 || l == 0) return OS_OK;
+    const BlockList all = mask_to_list(~0ull, p->P);
+    return launch_pair_bf16(At, ldat, BtT, ldbt, m, l, z, p->b, all, 1.f, beta, C, ldc, as_stream(stream),
+                            block_masks, bm, bn, p->P);
 }

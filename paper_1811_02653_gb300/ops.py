@@ -100,6 +100,8 @@ def load_library(path: str | None = None):
                                                            ctypes.POINTER(sz)]),
             "oversketch_matmul_host": (st, [vp, vp, st, i64, vp, st, i64, vp, i64, i64, i64, i64, u64,
                                             ctypes.POINTER(_Opts), vp, sz, vp]),
+            "oversketch_gemm_masked_blocks": (st, [vp, vp, i64, vp, i64, i64, i64, vp, i64, i64, f32, vp,
+                                                   i64, vp]),
             "oversketch_sketch_size": (st, [ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, i32,
                                             ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "oversketch_batch_create": (st, [ctypes.POINTER(_Problem), i32, st, st, st, sz, i32, vp, pp]),
@@ -129,7 +131,8 @@ def _sigs_names():
             "oversketch_gemm_bf16", "oversketch_select_transpose", "oversketch_cast",
             "oversketch_batch_create", "oversketch_batch_run", "oversketch_batch_info",
             "oversketch_batch_destroy", "oversketch_sketch_left_sparse",
-            "oversketch_matmul_host_workspace_size", "oversketch_matmul_host", "oversketch_sketch_size"]
+            "oversketch_matmul_host_workspace_size", "oversketch_matmul_host", "oversketch_sketch_size",
+            "oversketch_gemm_masked_blocks"]
 
 
 def _check(status: int, what: str):
@@ -363,6 +366,19 @@ def gemm_masked(p: Plan, At, BtT, mask: int, alpha=None, beta=0.0, C=None, a_sca
         p.handle, _ptr(At), At.stride(0), _ptr(a_scales), _ptr(BtT), BtT.stride(0), _ptr(b_scales),
         _dtype_code(dtype) if dtype is not None else _dt(At), m, l, mask, alpha, beta, _ptr(C), C.stride(0),
         _stream(stream)), "oversketch_gemm_masked")
+    return C
+
+
+def gemm_masked_blocks(p: Plan, At, BtT, block_masks, bm: int, bn: int, beta=0.0, C=None, stream=None):
+    """C with Alg. 3's termination rule per bm x bn block of C: block (i, j) sums its
+    own kept sketch blocks block_masks[i, j] (int64 CUDA tensor of bit masks), 1/k_ij."""
+    m, l = At.shape[0], BtT.shape[0]
+    if C is None:
+        C = torch.empty((m, l), dtype=torch.float32, device=At.device)
+    bmask = block_masks.contiguous()
+    _check(load_library().oversketch_gemm_masked_blocks(
+        p.handle, _ptr(At), At.stride(0), _ptr(BtT), BtT.stride(0), m, l, _ptr(bmask), bm, bn, beta, _ptr(C),
+        C.stride(0), _stream(stream)), "oversketch_gemm_masked_blocks")
     return C
 
 
