@@ -1,0 +1,63 @@
+"""CPU reference of the interior-point LP of Sec. 5.2 -- test infrastructure only.
+
+The LP   minimize c^T x  subject to  A x <= b   (A: n x m, n > m)
+is solved by the logarithmic barrier method of Sec. 5.2: Newton's method on
+f(x) = tau c^T x - sum_i log(b_i - a_i x), with tau doubled every `every`
+iterations, using the exact Hessian A^T diag(1/(b - A x)^2) A and the gradient
+tau c + sum_i a_i^T / (b_i - a_i x).  The step size eta comes from a
+backtracking line search that keeps every slack positive (Armijo condition
+with parameter 1/4, halving).  Plain FP64 numpy; shares no code with the GPU
+solver.  The pinned fact: after the last centring step at barrier weight tau
+the objective is within n / tau of the LP optimum (the barrier's duality gap).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def barrier_objective(A, b, c, x, tau):
+    s = b - A @ x
+    if np.any(s <= 0):
+        return np.inf
+    return tau * float(c @ x) - float(np.sum(np.log(s)))
+
+
+def barrier_lp(A, b, c, x0, iters=100, tau0=1.0, every=10, hessian=None):
+    """Newton iterations of the barrier method; returns (x, objective c^T x per
+    iteration).  `hessian(x, s, t)` may replace the exact Hessian (iteration t,
+    slacks s); the default is A^T diag(1/s^2) A."""
+    A = np.asarray(A, np.float64)
+    b = np.asarray(b, np.float64)
+    c = np.asarray(c, np.float64)
+    x = np.asarray(x0, np.float64).copy()
+    hist = []
+    for t in range(iters):
+        tau = tau0 * 2.0 ** (t // every)
+        s = b - A @ x
+        g = tau * c + A.T @ (1.0 / s)
+        H = hessian(x, s, t) if hessian is not None else (A.T * (1.0 / s ** 2)) @ A
+        dx = -np.linalg.solve(0.5 * (H + H.T), g)
+        f0 = barrier_objective(A, b, c, x, tau)
+        eta, slope = 1.0, float(g @ dx)
+        while eta > 1e-12:
+            xn = x + eta * dx
+            fn = barrier_objective(A, b, c, xn, tau)
+            if np.isfinite(fn) and fn <= f0 + 0.25 * eta * slope:
+                break
+            eta *= 0.5
+        if eta > 1e-12:
+            x = x + eta * dx
+        hist.append(float(c @ x))
+    return x, hist
+
+
+def synthetic_lp(n, m, seed):
+    """A bounded, strictly feasible LP: A ~ N(0, 1/m), b = 1 + |N(0,1)| (x = 0 is
+    strictly feasible), c = -A^T y with y >= 0 (c^T x >= -y^T b on the feasible set,
+    so the LP is bounded below)."""
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((n, m)) / np.sqrt(m)
+    b = 1.0 + np.abs(g.standard_normal(n))
+    y = np.abs(g.standard_normal(n)) * (g.random(n) < 0.05)
+    c = -(A.T @ y)
+    return A, b, c
