@@ -701,6 +701,75 @@ def run_autograd(args):
     return 0
 
 
+def run_lp(args):
+    """Sec. 5.2's LP at the paper's proportions: n = 40b constraints, m = 5b
+    variables, sketch dimension z = 20b (P = 20 blocks of width b = 1024), Hessian
+    blocks b x b.  The timed step is the sketched Hessian A^T D A of one Newton
+    iteration (right sketch of A with row scale 1/s, then the per-block masked GEMM
+    with one straggler ignored per block); the 100-iteration barrier runs
+    (unsketched BF16 Hessian, e = 0, e = 1 per block, e = 1 shared) follow."""
+    import torch
+    from paper_1811_02653_gb300 import build, lp, ops
+    from paper_1811_02653_gb300 import workloads as W
+    world, rank, _ = _init_dist()
+    build.build()
+    peaks, peak_kind = _peaks()
+    blk, P = 1024, 20
+    NC, MV = 40 * blk, 5 * blk
+    nb = MV // blk
+    A, bvec, c = W.lp_instance(NC, MV, 1006)
+    solver = lp.SketchedBarrierLP(A, bvec, c, blk=blk, N=P - 1, e=1, seed=0)
+    del A
+    per_block = lambda t: W.straggler_block_masks(P, 1, nb, nb, 11, t)
+    shared = lambda t: W.straggler_block_masks(P, 1, nb, nb, 11, t, shared=True)
+    runs, x_end = {}, None
+    solver.solve(iters=3)                      # cuSOLVER / cuBLAS handles and workspaces
+    for name, exact, masks in [("exact_bf16_hessian", True, None), ("e0", False, None),
+                               ("e1_per_block", False, per_block), ("e1_shared", False, shared)]:
+        solver.exact = exact
+        x, h = solver.solve(iters=args.lp_iters, block_masks=masks, timing=True)
+        if name == "e0":
+            x_end = x
+        runs[name] = {"final_objective": h.objective[-1], "iter_ms_mean": statistics.mean(h.iter_ms),
+                      "hessian_ms_mean": statistics.mean(h.hessian_ms), "shifted_systems": h.shifts,
+                      "objective_at_stage_ends": [h.objective[k] for k in range(9, len(h.objective), 10)]}
+    f_ref = runs["exact_bf16_hessian"]["final_objective"]
+    for r in runs.values():
+        r["rel_diff_vs_exact_hessian"] = abs(r["final_objective"] - f_ref) / abs(f_ref)
+    solver.exact = False
+    s = (solver.b - solver.A64 @ x_end)
+    d = (1.0 / s).float()
+    masks = torch.from_numpy(per_block(0)).cuda()
+
+    def sketch():
+        ops.sketch_right(solver.plan, solver.A, "bf16", out=solver.Ask, workspace=solver.ws, row_scale=d)
+
+    def gemm():
+        ops.gemm_masked_blocks(solver.plan, solver.Ask, solver.Ask, masks, blk, blk, C=solver.H)
+
+    ms, per, clk = _time_phases([("sketch", sketch), ("gemm", gemm)], args.steps, args.warmup, world)
+    value = _job_value(2.0 * MV * MV * NC, ms, world)
+    kept = P - 1
+    flop = 2.0 * MV * MV * kept * blk
+    ach = flop / (per["gemm"] * 1e-3) / 1e12
+    pk = peaks.get("bf16_tflops")
+    roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk if pk else None,
+            "traffic": None, "kernel": "gemm_pair_bf16_kernel (BF16, cta_group::2, per-block masks)",
+            "peak_source": f"bf16_tflops burst, {peak_kind} (MEASURED_PEAKS.json)",
+            "algorithmic_per_launch": {"flop": flop, "note": "2 m^2 k b, k = 19 kept blocks per block of H"}}
+    cfg = {"workload": f"lp hessian A^T D A, A {NC}x{MV} (n = 40b constraints, m = 5b variables), "
+                       f"b={blk}, P={P} (z = 20b), one straggler per Hessian block",
+           "n": NC, "m": MV, "b": blk, "P": P, "e_per_block": 1, "gemm_dtype": "bf16", "input_dtype": "f32",
+           "metric_note": "effective flop = 2 m^2 n (the exact Hessian)",
+           "l2": "A (839 MB FP32) larger than L2; no flush needed", "parallelism": f"replicas{world}",
+           "lp_iterations": args.lp_iters, "tau": "1, doubled every 10 iterations"}
+    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, None, None, None, clk, None, world,
+                 lp_runs=runs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -713,11 +782,12 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-GEMM comparison")
-    ap.add_argument("--workload", default="square", choices=["square", "hessian", "batched", "autograd"],
+    ap.add_argument("--workload", default="square", choices=["square", "hessian", "batched", "autograd", "lp"],
                     help="square (default: the headline line), or another workload of the suite")
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
     ap.add_argument("--recompute", action="store_true", help="autograd: recompute the sketches in backward")
     ap.add_argument("--dense-sketch", action="store_true", help="hessian: sketch A with the dense gather path")
+    ap.add_argument("--lp-iters", type=int, default=100, help="lp: barrier iterations per run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -727,6 +797,8 @@ def main():
         return run_batched(args)
     if args.workload == "autograd":
         return run_autograd(args)
+    if args.workload == "lp":
+        return run_lp(args)
     return run_ours(args)
 
 

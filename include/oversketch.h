@@ -157,14 +157,19 @@ OS_API os_status oversketch_sketch_size(double eps, double theta, int32_t b, dou
  *     Columns of blocks not listed are left untouched (the paper's remark
  *     that blocks missed while sketching become stragglers of the product).
  *   workspace: device memory of at least oversketch_sketch_workspace(plan, m,
- *     a_t) bytes; the operand is packed there strip-major (32 free indices
+ *     a_t) bytes; the operand is packed there strip-major (128 free indices
  *     per strip, n rows each) before the bucket gather.
  * oversketch_sketch_right:
- *   BtT[c, j*b + q] = sum_{i : h_j(i) = q} sigma_j(i) * B[i, c]
+ *   BtT[c, j*b + q] = sum_{i : h_j(i) = q} sigma_j(i) * s_i * B[i, c]
  *   B: n x l (ldb >= l); BtT: l x z (ldbt >= z); FP8 scales as above with
  *   OS_FP8_SCALE_LD(l) entries per slice;
+ *   row_scale: n FP32 device values s_i, or NULL (s_i = 1): S^T diag(s) B,
+ *     e.g. the Hessian square root diag(1/s) A of Sec. 5.2 without forming it;
+ *     a term is s_i * B[i, c] rounded once, then added;
  *   block_mask as above; workspace of oversketch_sketch_workspace(plan, l, b_t)
- *   bytes.
+ *   bytes (an FP32 B with 16-byte aligned rows is gathered in place in
+ *   128-column strips and only a ragged remainder of fewer than 128 columns
+ *   is packed there).
  * Errors: OS_ERR_INVALID_ARG (null pointers, ld too small, out pointers or
  *   ld not 16-byte aligned), OS_ERR_DTYPE, OS_ERR_UNSUPPORTED,
  *   OS_ERR_WORKSPACE, OS_ERR_CUDA (launch failure).
@@ -177,8 +182,8 @@ OS_API os_status oversketch_sketch_left(oversketch_plan_t plan, const void *A, o
                                  size_t ws_bytes, void *stream);
 OS_API os_status oversketch_sketch_right(oversketch_plan_t plan, const void *B, os_dtype b_t, int64_t l,
                                   int64_t ldb, void *BtT, os_dtype out_t, int64_t ldbt,
-                                  float *scales, uint64_t block_mask, void *workspace,
-                                  size_t ws_bytes, void *stream);
+                                  float *scales, const float *row_scale, uint64_t block_mask,
+                                  void *workspace, size_t ws_bytes, void *stream);
 
 /* -------------------------------------------------------------------------
  * Left sketch of a sparse operand stored dense (Alg. 4 step 3 over the

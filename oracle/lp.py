@@ -4,11 +4,16 @@ The LP   minimize c^T x  subject to  A x <= b   (A: n x m, n > m)
 is solved by the logarithmic barrier method of Sec. 5.2: Newton's method on
 f(x) = tau c^T x - sum_i log(b_i - a_i x), with tau doubled every `every`
 iterations, using the exact Hessian A^T diag(1/(b - A x)^2) A and the gradient
-tau c + sum_i a_i^T / (b_i - a_i x).  The step size eta comes from a
-backtracking line search that keeps every slack positive (Armijo condition
-with parameter 1/4, halving).  Plain FP64 numpy; shares no code with the GPU
-solver.  The pinned fact: after the last centring step at barrier weight tau
-the objective is within n / tau of the LP optimum (the barrier's duality gap).
+tau c + sum_i a_i^T / (b_i - a_i x).  The Newton system uses the symmetric
+part of the Hessian, Jacobi-equilibrated; when that is not positive definite (a
+sketched Hessian whose blocks keep different sketch blocks need not be) the
+smallest shift in 0, 1e-8, 1e-7, ... times the identity that makes it so is
+added -- the paper does not say how an indefinite system is treated, this is
+the reading both solvers share.  The step size eta comes from a backtracking
+line search that keeps every slack positive (Armijo condition with parameter
+1/4, halving).  Plain FP64 numpy; shares no code with the GPU solver.  The
+pinned fact: after the last centring step at barrier weight tau the objective
+is within n / tau of the LP optimum (the barrier's duality gap).
 """
 from __future__ import annotations
 
@@ -20,6 +25,23 @@ def barrier_objective(A, b, c, x, tau):
     if np.any(s <= 0):
         return np.inf
     return tau * float(c @ x) - float(np.sum(np.log(s)))
+
+
+def newton_direction(H, g):
+    """-(H_sym + shift D)^{-1} g with D = diag(H_sym) and the smallest shift of
+    0, 1e-8, 1e-7, ... for which the equilibrated system is positive definite."""
+    Hs = 0.5 * (H + H.T)
+    d = 1.0 / np.sqrt(np.maximum(np.diag(Hs), np.finfo(np.float64).tiny))
+    He = Hs * d[:, None] * d[None, :]
+    shift = 0.0
+    while True:
+        try:
+            L = np.linalg.cholesky(He + shift * np.eye(len(d)))
+            break
+        except np.linalg.LinAlgError:
+            shift = 1e-8 if shift == 0.0 else shift * 10.0
+    y = np.linalg.solve(L.T, np.linalg.solve(L, g * d))
+    return -(y * d)
 
 
 def barrier_lp(A, b, c, x0, iters=100, tau0=1.0, every=10, hessian=None):
@@ -36,7 +58,7 @@ def barrier_lp(A, b, c, x0, iters=100, tau0=1.0, every=10, hessian=None):
         s = b - A @ x
         g = tau * c + A.T @ (1.0 / s)
         H = hessian(x, s, t) if hessian is not None else (A.T * (1.0 / s ** 2)) @ A
-        dx = -np.linalg.solve(0.5 * (H + H.T), g)
+        dx = newton_direction(H, g)
         f0 = barrier_objective(A, b, c, x, tau)
         eta, slope = 1.0, float(g @ dx)
         while eta > 1e-12:
@@ -50,14 +72,3 @@ def barrier_lp(A, b, c, x0, iters=100, tau0=1.0, every=10, hessian=None):
         hist.append(float(c @ x))
     return x, hist
 
-
-def synthetic_lp(n, m, seed):
-    """A bounded, strictly feasible LP: A ~ N(0, 1/m), b = 1 + |N(0,1)| (x = 0 is
-    strictly feasible), c = -A^T y with y >= 0 (c^T x >= -y^T b on the feasible set,
-    so the LP is bounded below)."""
-    g = np.random.default_rng(seed)
-    A = g.standard_normal((n, m)) / np.sqrt(m)
-    b = 1.0 + np.abs(g.standard_normal(n))
-    y = np.abs(g.standard_normal(n)) * (g.random(n) < 0.05)
-    c = -(A.T @ y)
-    return A, b, c

@@ -17,7 +17,7 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
                            cudaStream_t st);
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
                             void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
-                            void *ws, size_t ws_bytes, cudaStream_t st);
+                            void *ws, size_t ws_bytes, cudaStream_t st, const float *row_scale = nullptr);
 bool sketch_left_sparse_fits(const Plan *p, uint64_t block_mask);
 os_status sketch_left_sparse_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda, void *At,
                                   os_dtype out_t, int64_t ldat, float *scales, const float *col_scale,

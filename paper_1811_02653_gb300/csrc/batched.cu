@@ -31,7 +31,7 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
                            uint64_t block_mask, void *ws, size_t ws_bytes, cudaStream_t st);
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb, void *BtT,
                             os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask, void *ws,
-                            size_t ws_bytes, cudaStream_t st);
+                            size_t ws_bytes, cudaStream_t st, const float *row_scale = nullptr);
 size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t);
 
 namespace {

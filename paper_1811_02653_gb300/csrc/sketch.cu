@@ -486,21 +486,22 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *co
 // Gather straight from a row-major FP32 operand in 128-wide strips (512-byte row
 // pieces: one address translation per 512 bytes is cheap enough that no
 // packing pass is needed).  F must be a multiple of 128.
-os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, void *Yt, os_dtype out_t,
-                               int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask, cudaStream_t st,
-                               int64_t plane_rows = 0) {
+os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, const float *row_scale,
+                               void *Yt, os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld,
+                               uint64_t block_mask, cudaStream_t st, int64_t plane_rows = 0) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
+    const float *rs = row_scale;
     switch (out_t) {
         case OS_F32:
-            return launch_gather_t<float, float, kGatherQT, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks, st);
+            return launch_gather_t<float, float, kGatherQT, 1>(p, X, kStrip, ldx, F, rs, Yt, ldy, nullptr, scale_ld, blocks, st);
         case OS_BF16:
-            return launch_gather_t<float, __nv_bfloat16, kGatherQT, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld,
+            return launch_gather_t<float, __nv_bfloat16, kGatherQT, 1>(p, X, kStrip, ldx, F, rs, Yt, ldy, nullptr, scale_ld,
                                                                 blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_t<float, __nv_fp8_e4m3, 32, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<float, __nv_fp8_e4m3, 32, 1>(p, X, kStrip, ldx, F, rs, Yt, ldy, scales, scale_ld,
                                                                  blocks, st);
         case OS_TF32X2:
-            return launch_gather_t<float, Tf32Pair, kGatherQT, 1>(p, X, kStrip, ldx, F, nullptr, Yt, ldy, nullptr, scale_ld, blocks,
+            return launch_gather_t<float, Tf32Pair, kGatherQT, 1>(p, X, kStrip, ldx, F, rs, Yt, ldy, nullptr, scale_ld, blocks,
                                                            st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
@@ -582,7 +583,7 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
 
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
                             void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
-                            void *ws, size_t ws_bytes, cudaStream_t st) {
+                            void *ws, size_t ws_bytes, cudaStream_t st, const float *row_scale) {
     if (!p || !B || l < 0) return OS_ERR_INVALID_ARG;
     if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (b_t != OS_F32 && b_t != OS_BF16) return OS_ERR_DTYPE;
@@ -595,26 +596,26 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
                         l >= kStrip;
     if (direct) {
         const int64_t lf = l / kStrip * kStrip;
-        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, BtT, out_t, ldbt, scales, fp8_scale_ld(l),
-                                     block_mask, st, l));
+        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, row_scale, BtT, out_t, ldbt, scales,
+                                     fp8_scale_ld(l), block_mask, st, l));
         if (lf == l) return OS_OK;
         if (!ws || ws_bytes < sketch_workspace_bytes(p, l - lf, b_t)) return OS_ERR_WORKSPACE;
         float *Xs = (float *)ws_base(ws);
         OSK_TRY(launch_pack_rows<float>((const float *)B + lf, ldb, p->n, l - lf, Xs, st));
         char *yt = (char *)BtT + (size_t)lf * ldbt * dtype_size(out_t);
         float *sc = scales ? scales + lf : nullptr;   // slice-major: the remainder's rows start at lf
-        return launch_gather<float>(p, Xs, l - lf, nullptr, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask, st,
+        return launch_gather<float>(p, Xs, l - lf, row_scale, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask, st,
                                     l);
     }
     if (!ws || ws_bytes < sketch_workspace_bytes(p, l, b_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);
     if (b_t == OS_F32) {
         OSK_TRY(launch_pack_rows<float>((const float *)B, ldb, p->n, l, (float *)Xs, st));
-        return launch_gather<float>(p, (const float *)Xs, l, nullptr, BtT, out_t, ldbt, scales, fp8_scale_ld(l),
+        return launch_gather<float>(p, (const float *)Xs, l, row_scale, BtT, out_t, ldbt, scales, fp8_scale_ld(l),
                                     block_mask, st, l);
     }
     OSK_TRY(launch_pack_rows<__nv_bfloat16>((const __nv_bfloat16 *)B, ldb, p->n, l, (__nv_bfloat16 *)Xs, st));
-    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, l, nullptr, BtT, out_t, ldbt, scales,
+    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, l, row_scale, BtT, out_t, ldbt, scales,
                                         fp8_scale_ld(l), block_mask, st, l);
 }
 
@@ -682,10 +683,11 @@ extern "C" os_status oversketch_sketch_left(oversketch_plan_t plan, const void *
 
 extern "C" os_status oversketch_sketch_right(oversketch_plan_t plan, const void *B, os_dtype b_t,
                                              int64_t l, int64_t ldb, void *BtT, os_dtype out_t,
-                                             int64_t ldbt, float *scales, uint64_t block_mask,
-                                             void *workspace, size_t ws_bytes, void *stream) {
+                                             int64_t ldbt, float *scales, const float *row_scale,
+                                             uint64_t block_mask, void *workspace, size_t ws_bytes,
+                                             void *stream) {
     return sketch_right_impl(reinterpret_cast<const Plan *>(plan), B, b_t, l, ldb, BtT, out_t, ldbt,
-                             scales, block_mask, workspace, ws_bytes, as_stream(stream));
+                             scales, block_mask, workspace, ws_bytes, as_stream(stream), row_scale);
 }
 
 extern "C" os_status oversketch_unsketch_cols(oversketch_plan_t plan, const float *T, int64_t m,

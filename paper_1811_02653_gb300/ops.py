@@ -81,7 +81,7 @@ def load_library(path: str | None = None):
             "oversketch_plan_destroy": (st, [vp]),
             "oversketch_sketch_workspace": (st, [vp, i64, st, ctypes.POINTER(sz)]),
             "oversketch_sketch_left": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, u64, vp, sz, vp]),
-            "oversketch_sketch_right": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, u64, vp, sz, vp]),
+            "oversketch_sketch_right": (st, [vp, vp, st, i64, i64, vp, st, i64, vp, vp, u64, vp, sz, vp]),
             "oversketch_gemm_masked": (st, [vp, vp, i64, vp, vp, i64, vp, st, i64, i64, u64, f32, f32,
                                             vp, i64, vp]),
             "oversketch_workspace_size": (st, [vp, i64, i64, st, st, ctypes.POINTER(_Opts), ctypes.POINTER(sz)]),
@@ -336,8 +336,8 @@ def sketch_left_sparse(p: Plan, A: torch.Tensor, out_dtype="f32", col_scale=None
 
 
 def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=None, block_mask=0,
-                 workspace=None, stream=None):
-    """B~^T = (S^T B)^T (l x z, K-major); returns (BtT, scales or None)."""
+                 workspace=None, stream=None, row_scale=None):
+    """B~^T = (S^T diag(row_scale) B)^T (l x z, K-major); returns (BtT, scales or None)."""
     ldb = _rowmajor(B, "B")
     l = B.shape[1]
     od = _dtype_code(out_dtype)
@@ -348,8 +348,8 @@ def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=Non
         scales = torch.empty(_fp8_scales_shape(l, p.z), dtype=torch.float32, device=B.device)
     workspace = _workspace(p, l, B.dtype, B.device, workspace)
     _check(load_library().oversketch_sketch_right(
-        p.handle, _ptr(B), _dt(B), l, ldb, _ptr(out), od, out.stride(0), _ptr(scales), block_mask,
-        _ptr(workspace), workspace.numel(), _stream(stream)), "oversketch_sketch_right")
+        p.handle, _ptr(B), _dt(B), l, ldb, _ptr(out), od, out.stride(0), _ptr(scales), _ptr(row_scale),
+        block_mask, _ptr(workspace), workspace.numel(), _stream(stream)), "oversketch_sketch_right")
     return out, scales
 
 

@@ -262,3 +262,38 @@ def scaled(w: Workload, **kw) -> Workload:
     d = dict(w.__dict__)
     d.update(kw)
     return Workload(**d)
+
+
+def lp_instance(n: int, m: int, seed: int = 1006, density: float = 0.05):
+    """The LP  min c^T x  s.t.  A x <= b  of Sec. 5.2 (A: n x m, n > m), drawn so
+    that it is strictly feasible and bounded: A ~ N(0, 1/m) rounded to FP32,
+    b = 1 + |N(0,1)| (x = 0 is strictly feasible), and c = -A^T y for a
+    nonnegative y with about `density` n nonzeros (then c^T x >= -y^T b on the
+    feasible set).  Returns (A float32 n x m, b float64 n, c float64 m)."""
+    A = gaussian_rows(seed, _S_LEFT, range(n), m, std=1.0 / math.sqrt(m))
+    g = _rng(seed, _S_D, 0)
+    b = 1.0 + np.abs(g.standard_normal(n))
+    y = np.abs(g.standard_normal(n)) * (g.random(n) < density)
+    c = -(A.astype(np.float64).T @ y)
+    return A, b, c
+
+
+def straggler_block_masks(P: int, e: int, rows: int, cols: int, seed: int, it: int,
+                          shared: bool = False) -> np.ndarray:
+    """rows x cols int64 bit masks over P sketch blocks, each with e bits cleared
+    at positions drawn uniformly without replacement, independently per block of
+    C and per iteration `it`: the e workers that straggle on that block.  With
+    `shared` every block gets the first block's mask (one straggler set for the
+    whole product)."""
+    g = _rng(seed, _S_MASKPOS, it)
+    full = (1 << P) - 1
+    out = np.empty((rows, cols), dtype=np.int64)
+    for i in range(rows):
+        for j in range(cols):
+            msk = full
+            for pos in g.choice(P, size=e, replace=False):
+                msk &= ~(1 << int(pos))
+            out[i, j] = np.int64(msk - (1 << 64) if msk >= 1 << 63 else msk)
+    if shared:
+        out[:] = out[0, 0]
+    return out

@@ -120,6 +120,27 @@ def test_sketch_col_scale(ops):
     assert_fp32_within(At.cpu().numpy(), ref, bd)
 
 
+@pytest.mark.parametrize("l,in_dtype", [(384, None),                 # in-place strips
+                                         (301, None),                 # in-place strips + packed remainder
+                                         (70, torch.bfloat16)])       # packed BF16 operand
+def test_sketch_right_row_scale(ops, l, in_dtype):
+    # S^T diag(s) B: the right sketch with a scale per sketched index i equals the
+    # left sketch of B^T with that column scale
+    n, b, N, e = 3000, 256, 3, 1
+    rng = np.random.default_rng(l)
+    B = rng.standard_normal((n, l)).astype(np.float32)
+    rs = np.sqrt(10.0 ** rng.uniform(-6, 6, n)).astype(np.float32)
+    Bd = _dev(B, in_dtype)
+    B64 = Bd.float().cpu().numpy()
+    p = ops.plan(n, b, N, e, 2)
+    h, s = oracle.hash_tables(n, b, N, e, 2)
+    BtT, _ = ops.sketch_right(p, Bd, "f32", row_scale=_dev(rs))
+    ref, bd = sketch_bounds_left(np.ascontiguousarray(B64.T), h, s, b, rs)
+    assert_fp32_within(BtT.cpu().numpy(), ref, bd)
+    Bb, _ = ops.sketch_right(p, Bd, "bf16", row_scale=_dev(rs))
+    assert_bf16_within(Bb.float().cpu().numpy(), ref, bd)
+
+
 @pytest.mark.parametrize("m,n,l,b,N,e", [(512, 4096, 512, 256, 4, 1), (200, 3000, 70, 128, 2, 1)])
 def test_sketch_bf16_parity(ops, m, n, l, b, N, e):
     rng = np.random.default_rng(11)

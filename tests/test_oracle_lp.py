@@ -5,12 +5,13 @@ import numpy as np
 import pytest
 
 from oracle import lp
+from paper_1811_02653_gb300 import workloads
 
 
 def test_barrier_reaches_the_lp_optimum():
     opt = pytest.importorskip("scipy.optimize")
     n, m = 400, 20
-    A, b, c = lp.synthetic_lp(n, m, 3)
+    A, b, c = workloads.lp_instance(n, m, 3)
     x, hist = lp.barrier_lp(A, b, c, np.zeros(m), iters=100, tau0=1.0, every=10)
     res = opt.linprog(c, A_ub=A, b_ub=b, bounds=[(None, None)] * m, method="highs")
     assert res.status == 0
@@ -22,7 +23,59 @@ def test_barrier_reaches_the_lp_optimum():
 
 def test_barrier_objective_decreases_per_centring_stage():
     n, m = 300, 15
-    A, b, c = lp.synthetic_lp(n, m, 4)
+    A, b, c = workloads.lp_instance(n, m, 4)
     _, hist = lp.barrier_lp(A, b, c, np.zeros(m), iters=60, every=10)
     ends = [hist[k] for k in range(9, 60, 10)]
     assert all(ends[i + 1] <= ends[i] + 1e-9 for i in range(len(ends) - 1))
+
+
+def _sketched_hessian(A, blk, P, masks_of, cb):
+    import oracle
+    n = A.shape[0]
+    h, sg = oracle.hash_tables(n, blk, P - 1, 1, 0)
+
+    def hess(x, s, t):
+        Ask = oracle.sketch_left(A.T, h, sg, blk, col_scale=1.0 / s)
+        return oracle.masked_product_blocks(Ask, Ask.T, blk, masks_of(t).tolist(), cb, cb)
+    return hess
+
+
+def test_gram_form_sketched_hessian_tracks_the_exact_newton_path():
+    """With one kept set for the whole Hessian the sketched Hessian is the Gram
+    matrix (S D^{1/2} A)^T (S D^{1/2} A) / k: positive semidefinite, and with the
+    sketch dimension n/2 of Sec. 5.2 the barrier path ends where the exact one does."""
+    n, m, blk, P = 2048, 512, 128, 8
+    A, b, c = workloads.lp_instance(n, m, 5)
+    A = A.astype(np.float64)
+    _, exact = lp.barrier_lp(A, b, c, np.zeros(m))
+    masks = lambda t: workloads.straggler_block_masks(P, 1, 2, 2, 11, t, shared=True)
+    _, sk = lp.barrier_lp(A, b, c, np.zeros(m), hessian=_sketched_hessian(A, blk, P, masks, 256))
+    assert abs(sk[-1] - exact[-1]) <= 2e-3 * abs(exact[-1])
+
+
+def test_per_block_stragglers_break_the_gram_form_and_the_shift_keeps_descent():
+    """Independent kept sets per block of the Hessian (Alg. 3 applied per block)
+    give a symmetric part that is indefinite at most iterations; the shifted
+    Newton system still yields descent steps, so the iterates stay strictly
+    feasible and the objective improves from stage to stage."""
+    n, m, blk, P = 2048, 512, 128, 8
+    A, b, c = workloads.lp_instance(n, m, 5)
+    A = A.astype(np.float64)
+    masks = lambda t: workloads.straggler_block_masks(P, 1, 2, 2, 11, t)
+    hess = _sketched_hessian(A, blk, P, masks, 256)
+    t = next(t for t in range(100) if masks(t)[0, 1] != masks(t)[1, 0])
+    H = hess(np.zeros(m), b.copy(), t)
+    assert np.abs(H - H.T).max() > 1e-3 * np.abs(H).max()
+    x, hist = lp.barrier_lp(A, b, c, np.zeros(m), hessian=hess)
+    assert np.all(b - A @ x > 0)
+    ends = [hist[k] for k in range(9, 100, 10)]
+    assert ends[-1] < ends[0] and ends[-1] < ends[4]
+
+
+def test_straggler_masks():
+    m = workloads.straggler_block_masks(20, 1, 5, 5, 3, 0)
+    assert m.shape == (5, 5) and all(bin(int(v)).count("1") == 19 for v in m.ravel())
+    assert len(set(m.ravel().tolist())) > 1
+    s = workloads.straggler_block_masks(20, 2, 5, 5, 3, 0, shared=True)
+    assert len(set(s.ravel().tolist())) == 1 and bin(int(s[0, 0])).count("1") == 18
+    assert (workloads.straggler_block_masks(20, 1, 5, 5, 3, 0) == m).all()
