@@ -723,9 +723,11 @@ def run_lp(args):
     per_block = lambda t: W.straggler_block_masks(P, 1, nb, nb, 11, t)
     shared = lambda t: W.straggler_block_masks(P, 1, nb, nb, 11, t, shared=True)
     runs, x_end = {}, None
-    solver.solve(iters=3)                      # cuSOLVER / cuBLAS handles and workspaces
-    for name, exact, masks in [("exact_bf16_hessian", True, None), ("e0", False, None),
-                               ("e1_per_block", False, per_block), ("e1_shared", False, shared)]:
+    if args.lp_iters > 0:
+        solver.solve(iters=3)                  # cuSOLVER / cuBLAS handles and workspaces
+    for name, exact, masks in ([("exact_bf16_hessian", True, None), ("e0", False, None),
+                                ("e1_per_block", False, per_block), ("e1_shared", False, shared)]
+                               if args.lp_iters > 0 else []):
         solver.exact = exact
         x, h = solver.solve(iters=args.lp_iters, block_masks=masks, timing=True)
         if name == "e0":
@@ -733,9 +735,12 @@ def run_lp(args):
         runs[name] = {"final_objective": h.objective[-1], "iter_ms_mean": statistics.mean(h.iter_ms),
                       "hessian_ms_mean": statistics.mean(h.hessian_ms), "shifted_systems": h.shifts,
                       "objective_at_stage_ends": [h.objective[k] for k in range(9, len(h.objective), 10)]}
-    f_ref = runs["exact_bf16_hessian"]["final_objective"]
-    for r in runs.values():
-        r["rel_diff_vs_exact_hessian"] = abs(r["final_objective"] - f_ref) / abs(f_ref)
+    if runs:
+        f_ref = runs["exact_bf16_hessian"]["final_objective"]
+        for r in runs.values():
+            r["rel_diff_vs_exact_hessian"] = abs(r["final_objective"] - f_ref) / abs(f_ref)
+    if x_end is None:                          # no barrier runs: time the Hessian at x = 0
+        x_end = torch.zeros(MV, dtype=torch.float64, device="cuda")
     solver.exact = False
     s = (solver.b - solver.A64 @ x_end)
     d = (1.0 / s).float()
@@ -753,10 +758,17 @@ def run_lp(args):
     flop = 2.0 * MV * MV * kept * blk
     ach = flop / (per["gemm"] * 1e-3) / 1e12
     pk = peaks.get("bf16_tflops")
-    roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk if pk else None,
-            "traffic": None, "kernel": "gemm_pair_bf16_kernel (BF16, cta_group::2, per-block masks)",
-            "peak_source": f"bf16_tflops burst, {peak_kind} (MEASURED_PEAKS.json)",
-            "algorithmic_per_launch": {"flop": flop, "note": "2 m^2 k b, k = 19 kept blocks per block of H"}}
+    roof_gemm = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                 "frac": ach / pk if pk else None, "traffic": None,
+                 "kernel": "gemm_pair_bf16_kernel (BF16, cta_group::2, per-block masks)",
+                 "peak_source": f"bf16_tflops burst, {peak_kind} (MEASURED_PEAKS.json)",
+                 "algorithmic_per_launch": {"flop": flop, "note": "2 m^2 k b, k = 19 kept blocks per block of H"}}
+    # the dominant kernel is the gather: A read once (FP32) and A~ written once (BF16)
+    gbytes = NC * MV * 4 + MV * P * blk * 2
+    roof = _hbm_roof(peaks, peak_kind, gbytes, per["sketch"],
+                     "sketch_gather_kernel (right sketch of A in place, row scale 1/s, BF16 out)")
+    roof["l2_gather_tbs"] = P * NC * MV * 4 / (per["sketch"] * 1e-3) / 1e12
+    roof["note"] = "every element of A reaches P = 20 buckets, one per sketch block: P |A| leaves the L2"
     cfg = {"workload": f"lp hessian A^T D A, A {NC}x{MV} (n = 40b constraints, m = 5b variables), "
                        f"b={blk}, P={P} (z = 20b), one straggler per Hessian block",
            "n": NC, "m": MV, "b": blk, "P": P, "e_per_block": 1, "gemm_dtype": "bf16", "input_dtype": "f32",
@@ -764,7 +776,7 @@ def run_lp(args):
            "l2": "A (839 MB FP32) larger than L2; no flush needed", "parallelism": f"replicas{world}",
            "lp_iterations": args.lp_iters, "tau": "1, doubled every 10 iterations"}
     line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, None, None, None, clk, None, world,
-                 lp_runs=runs)
+                 roofline_gemm=roof_gemm, lp_runs=runs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -787,7 +799,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
     ap.add_argument("--recompute", action="store_true", help="autograd: recompute the sketches in backward")
     ap.add_argument("--dense-sketch", action="store_true", help="hessian: sketch A with the dense gather path")
-    ap.add_argument("--lp-iters", type=int, default=100, help="lp: barrier iterations per run")
+    ap.add_argument("--lp-iters", type=int, default=100,
+                    help="lp: barrier iterations per run (0: time the Hessian at x = 0 only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

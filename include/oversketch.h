@@ -158,7 +158,9 @@ OS_API os_status oversketch_sketch_size(double eps, double theta, int32_t b, dou
  *     that blocks missed while sketching become stragglers of the product).
  *   workspace: device memory of at least oversketch_sketch_workspace(plan, m,
  *     a_t) bytes; the operand is packed there strip-major (128 free indices
- *     per strip, n rows each) before the bucket gather.
+ *     per strip, n rows each) before the bucket gather, and with a col_scale
+ *     the signed scales sigma_j(i) * s_i are laid out there in bucket-list
+ *     order first (one coalesced load per 32 gathered rows).
  * oversketch_sketch_right:
  *   BtT[c, j*b + q] = sum_{i : h_j(i) = q} sigma_j(i) * s_i * B[i, c]
  *   B: n x l (ldb >= l); BtT: l x z (ldbt >= z); FP8 scales as above with
@@ -169,7 +171,8 @@ OS_API os_status oversketch_sketch_size(double eps, double theta, int32_t b, dou
  *   block_mask as above; workspace of oversketch_sketch_workspace(plan, l, b_t)
  *   bytes (an FP32 B with 16-byte aligned rows is gathered in place in
  *   128-column strips and only a ragged remainder of fewer than 128 columns
- *   is packed there).
+ *   is packed there; with a row_scale the workspace also holds the signed
+ *   scales in bucket-list order).
  * Errors: OS_ERR_INVALID_ARG (null pointers, ld too small, out pointers or
  *   ld not 16-byte aligned), OS_ERR_DTYPE, OS_ERR_UNSUPPORTED,
  *   OS_ERR_WORKSPACE, OS_ERR_CUDA (launch failure).
@@ -218,8 +221,8 @@ OS_API os_status oversketch_sketch_left_sparse(oversketch_plan_t plan, const voi
  * not call cudaMalloc (it can synchronise the device).  The call allocates
  * nothing; the plan and the output are the caller's.
  *   - Limit: oversketch_sketch_workspace(plan, m, a_t) <= 32 MiB (for FP32
- *     that is ceil(m/128) * 128 * n * 4 bytes), else OS_ERR_WORKSPACE and no
- *     launch.
+ *     that is about ceil(m/128) * 128 * n * 4 bytes plus 4 * (N+e) * (n + 3b)
+ *     bytes of entry weights), else OS_ERR_WORKSPACE and no launch.
  *   - The first call on a device looks up the scratch array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

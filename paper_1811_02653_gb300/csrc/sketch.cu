@@ -93,7 +93,7 @@ template <typename InT, typename OutT, int QT, bool kScale, int SLOTS>
 __global__ void __launch_bounds__(kWarps * 32, 4)
 sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ldx, int64_t F,
                      const uint32_t *__restrict__ pperm, const uint32_t *__restrict__ poffs,
-                     int64_t pstride, int32_t b, int32_t z, const float *__restrict__ col_scale,
+                     int64_t pstride, int32_t b, int32_t z, const float *__restrict__ wts,
                      OutT *__restrict__ Yt, int64_t ldy, float *__restrict__ scales,
                      int64_t lds, BlockList blocks, int32_t tiles_per_block, int64_t plane_elems) {
     constexpr int SUBS = 32 / SLOTS;     // lanes per member
@@ -119,6 +119,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
     if (nb > 0) {
         const int cb = q0 - jblk * b + warp * QPW;        // first bucket (within the block)
         const uint32_t *pl = pperm + (int64_t)jblk * pstride;
+        const float *wl = kScale ? wts + (int64_t)jblk * pstride : nullptr;
         // group boundaries of the warp's buckets: lane t holds poffs[cb + t] / 4
         const uint32_t gbl = lane <= nb ? __ldg(poffs + (int64_t)jblk * (b + 1) + cb + lane) >> 2 : 0u;
         const uint32_t gend = __shfl_sync(0xffffffffu, gbl, nb);
@@ -132,21 +133,25 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
             const uint32_t pos = 4 * g + lane;
             return pos < 4 * gend ? __ldg(pl + pos) : kPadEntry;
         };
-        // GG groups (4*GG members) of the current bucket, entries in lanes 0 .. 4*GG-1 of e
-        auto batch = [&](auto gg, uint32_t e, float (&acc)[4]) {
+        // the signed scales sigma_j(i) s_i of the same 32 entries (scaled sketches)
+        auto load_weights = [&](uint32_t g) -> float {
+            if constexpr (!kScale) return 1.f;
+            const uint32_t pos = 4 * g + lane;
+            return pos < 4 * gend ? __ldg(wl + pos) : 0.f;
+        };
+        // GG groups (4*GG members) of the current bucket, entries in lanes 0 .. 4*GG-1
+        // of e, their signed scales in the same lanes of w
+        auto batch = [&](auto gg, uint32_t e, float w, float (&acc)[4]) {
             constexpr int GG = decltype(gg)::value;
             constexpr int KS = 4 * GG / SLOTS;            // member loads per lane
-            float sc_mine = 1.f;
-            if constexpr (kScale) sc_mine = e != kPadEntry ? __ldg(col_scale + (e & kIndexMask)) : 0.f;
             float v[KS][4];
             float wgt[KS];
 #pragma unroll
             for (int k = 0; k < KS; ++k) {
                 const uint32_t ent = __shfl_sync(0xffffffffu, e, k * SLOTS + slot);
-                // +-1 (or +-s_i) from the sign bit; padding reads the zero row
+                // +-1 from the sign bit (or the signed scale); padding reads the zero row
                 if constexpr (kScale) {
-                    const float sc = __shfl_sync(0xffffffffu, sc_mine, k * SLOTS + slot);
-                    wgt[k] = __uint_as_float(__float_as_uint(sc) ^ (ent & kSignBit));
+                    wgt[k] = __shfl_sync(0xffffffffu, w, k * SLOTS + slot);
                 } else {
                     wgt[k] = __uint_as_float(0x3f800000u | (ent & kSignBit));
                 }
@@ -175,12 +180,15 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
         // G/2, G/4, ..., 1 groups), prefetching the next 32 entries each time.
         uint32_t g = __shfl_sync(0xffffffffu, gbl, 0);
         uint32_t e_cur = load_entries(g);
+        float w_cur = load_weights(g);
         auto step = [&](auto gg, float (&acc)[4]) {
             constexpr int GG = decltype(gg)::value;
             const uint32_t e_nxt = load_entries(g + GG);
-            batch(gg, GG * 4 >= 32 ? e_cur : (lane < 4 * GG ? e_cur : kPadEntry), acc);
+            const float w_nxt = load_weights(g + GG);
+            batch(gg, GG * 4 >= 32 ? e_cur : (lane < 4 * GG ? e_cur : kPadEntry), w_cur, acc);
             g += GG;
             e_cur = e_nxt;
+            w_cur = w_nxt;
         };
         for (int t = 0; t < nb; ++t) {
             const uint32_t gE = __shfl_sync(0xffffffffu, gbl, t + 1);
@@ -415,9 +423,37 @@ __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     }
 }
 
+// The signed scale of every entry of the listed blocks' padded bucket lists,
+// in list order: w[j][pos] = sigma_j(i) * s_i for the entry (i, sigma) at pos
+// (0 for padding), so the gather loads the weights of 32 entries with one
+// coalesced load instead of 32 scattered loads of s.
+__global__ void __launch_bounds__(256) entry_weights_kernel(const uint32_t *__restrict__ pperm,
+                                                            const uint32_t *__restrict__ poffs, int64_t pstride,
+                                                            int32_t b, const float *__restrict__ s,
+                                                            BlockList blocks, float *__restrict__ w) {
+    const int j = blocks.idx[blockIdx.y];
+    const int64_t len = __ldg(poffs + (int64_t)j * (b + 1) + b);     // padded list length
+    const uint32_t *pl = pperm + (int64_t)j * pstride;
+    float *wl = w + (int64_t)j * pstride;
+    for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < len;
+         pos += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ent = __ldg(pl + pos);
+        wl[pos] = ent == kPadEntry ? 0.f
+                                   : __uint_as_float(__float_as_uint(__ldg(s + (ent & kIndexMask))) ^ (ent & kSignBit));
+    }
+}
+
+os_status launch_entry_weights(const Plan *p, const float *s, uint64_t block_mask, float *w, cudaStream_t st) {
+    const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
+    const int64_t per = (p->pstride + 255) / 256;
+    dim3 grid((unsigned)(per < 1024 ? per : 1024), (unsigned)blocks.count);
+    entry_weights_kernel<<<grid, 256, 0, st>>>(p->pperm, p->poffs, p->pstride, p->b, s, blocks, w);
+    return check_launch();
+}
+
 template <typename InT, typename OutT, int QT, int SLOTS>
 os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int64_t ldx, int64_t F,
-                          const float *col_scale, void *Yt, int64_t ldy, float *scales, int64_t scale_ld,
+                          const float *wts, void *Yt, int64_t ldy, float *scales, int64_t scale_ld,
                           const BlockList &blocks, cudaStream_t st, int64_t plane_elems = 0) {
     const int z = p->P * p->b;
     const int tpb = (p->b + QT - 1) / QT;
@@ -425,7 +461,7 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
     dim3 grid((unsigned)(tpb * blocks.count), (unsigned)((F + TF - 1) / TF));
     if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;
     const size_t smem = sizeof(float) * QT * (TF + 1);
-    auto k = col_scale ? sketch_gather_kernel<InT, OutT, QT, true, SLOTS>
+    auto k = wts ? sketch_gather_kernel<InT, OutT, QT, true, SLOTS>
                        : sketch_gather_kernel<InT, OutT, QT, false, SLOTS>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if constexpr (sizeof(OutT) == 1) {
@@ -444,11 +480,11 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         OSK_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, X, strip_stride, ldx, F, (const uint32_t *)p->pperm,
-                                        (const uint32_t *)p->poffs, p->pstride, p->b, z, col_scale, (OutT *)Yt, ldy,
+                                        (const uint32_t *)p->poffs, p->pstride, p->b, z, wts, (OutT *)Yt, ldy,
                                         scales, scale_ld, blocks, tpb, plane_elems));
     } else {
         k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
-                                          col_scale, (OutT *)Yt, ldy, scales, scale_ld, blocks, tpb, plane_elems);
+                                          wts, (OutT *)Yt, ldy, scales, scale_ld, blocks, tpb, plane_elems);
     }
     return check_launch();
 }
@@ -462,22 +498,22 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
 constexpr int kGatherQT = 16;
 
 template <typename InT>
-os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *col_scale, void *Yt,
+os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *wts, void *Yt,
                         os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask,
                         cudaStream_t st, int64_t plane_rows = 0) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
     const int64_t ss = p->n * kStrip;
     switch (out_t) {
         case OS_F32:
-            return launch_gather_t<InT, float, kGatherQT, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks, st);
+            return launch_gather_t<InT, float, kGatherQT, 1>(p, Xs, ss, kStrip, F, wts, Yt, ldy, scales, scale_ld, blocks, st);
         case OS_BF16:
-            return launch_gather_t<InT, __nv_bfloat16, kGatherQT, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<InT, __nv_bfloat16, kGatherQT, 1>(p, Xs, ss, kStrip, F, wts, Yt, ldy, scales, scale_ld,
                                                               blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_t<InT, __nv_fp8_e4m3, 32, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<InT, __nv_fp8_e4m3, 32, 1>(p, Xs, ss, kStrip, F, wts, Yt, ldy, scales, scale_ld,
                                                                blocks, st);
         case OS_TF32X2:
-            return launch_gather_t<InT, Tf32Pair, kGatherQT, 1>(p, Xs, ss, kStrip, F, col_scale, Yt, ldy, scales, scale_ld, blocks,
+            return launch_gather_t<InT, Tf32Pair, kGatherQT, 1>(p, Xs, ss, kStrip, F, wts, Yt, ldy, scales, scale_ld, blocks,
                                                          st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
@@ -486,22 +522,21 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *co
 // Gather straight from a row-major FP32 operand in 128-wide strips (512-byte row
 // pieces: one address translation per 512 bytes is cheap enough that no
 // packing pass is needed).  F must be a multiple of 128.
-os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, const float *row_scale,
+os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, const float *wts,
                                void *Yt, os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld,
                                uint64_t block_mask, cudaStream_t st, int64_t plane_rows = 0) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
-    const float *rs = row_scale;
-    switch (out_t) {
+        switch (out_t) {
         case OS_F32:
-            return launch_gather_t<float, float, kGatherQT, 1>(p, X, kStrip, ldx, F, rs, Yt, ldy, nullptr, scale_ld, blocks, st);
+            return launch_gather_t<float, float, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld, blocks, st);
         case OS_BF16:
-            return launch_gather_t<float, __nv_bfloat16, kGatherQT, 1>(p, X, kStrip, ldx, F, rs, Yt, ldy, nullptr, scale_ld,
+            return launch_gather_t<float, __nv_bfloat16, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld,
                                                                 blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_t<float, __nv_fp8_e4m3, 32, 1>(p, X, kStrip, ldx, F, rs, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<float, __nv_fp8_e4m3, 32, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, scales, scale_ld,
                                                                  blocks, st);
         case OS_TF32X2:
-            return launch_gather_t<float, Tf32Pair, kGatherQT, 1>(p, X, kStrip, ldx, F, rs, Yt, ldy, nullptr, scale_ld, blocks,
+            return launch_gather_t<float, Tf32Pair, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld, blocks,
                                                            st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
@@ -548,14 +583,36 @@ os_status check_out(const Plan *p, int64_t rows, void *Yt, os_dtype out_t, int64
 
 }  // namespace
 
-// Packed-strip workspace for F free indices: ceil(F/128) strips of n x 128 elements.
+namespace {
+size_t ws_align(size_t x) { return (x + 255) / 256 * 256; }
+// ceil(F/128) packed strips of n x 128 elements
+size_t strip_bytes(const Plan *p, int64_t F, os_dtype in_t) {
+    return (size_t)((F + kStrip - 1) / kStrip) * kStrip * (size_t)p->n * dtype_size(in_t);
+}
+}  // namespace
+
+// Sketch workspace for F free indices: the packed strips, then the signed
+// scale of every bucket-list entry (P x pstride FP32, used by scaled sketches).
 size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t) {
-    return (size_t)((F + kStrip - 1) / kStrip) * kStrip * (size_t)p->n * dtype_size(in_t) + 256;
+    return ws_align(strip_bytes(p, F, in_t)) + (size_t)p->P * p->pstride * sizeof(float) + 256;
 }
 
 namespace {
 void *ws_base(void *ws) {
     return reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+}
+// the entry weights of a workspace whose strips hold F free indices
+float *ws_weights(const Plan *p, void *ws, int64_t F, os_dtype in_t) {
+    return reinterpret_cast<float *>(reinterpret_cast<char *>(ws_base(ws)) + ws_align(strip_bytes(p, F, in_t)));
+}
+// the entry weights for scale s (NULL without a scale)
+os_status make_weights(const Plan *p, const float *s, uint64_t block_mask, float *w, const float **out,
+                       cudaStream_t st) {
+    *out = nullptr;
+    if (!s) return OS_OK;
+    OSK_TRY(launch_entry_weights(p, s, block_mask, w, st));
+    *out = w;
+    return OS_OK;
 }
 }  // namespace
 
@@ -571,13 +628,15 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
     if (m == 0) return OS_OK;
     if (!ws || ws_bytes < sketch_workspace_bytes(p, m, a_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);
+    const float *wts = nullptr;
+    OSK_TRY(make_weights(p, col_scale, block_mask, ws_weights(p, ws, m, a_t), &wts, st));
     if (a_t == OS_F32) {
         OSK_TRY(launch_pack_cols<float>((const float *)A, lda, m, p->n, (float *)Xs, st));
-        return launch_gather<float>(p, (const float *)Xs, m, col_scale, At, out_t, ldat, scales, fp8_scale_ld(m),
+        return launch_gather<float>(p, (const float *)Xs, m, wts, At, out_t, ldat, scales, fp8_scale_ld(m),
                                     block_mask, st, m);
     }
     OSK_TRY(launch_pack_cols<__nv_bfloat16>((const __nv_bfloat16 *)A, lda, m, p->n, (__nv_bfloat16 *)Xs, st));
-    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, m, col_scale, At, out_t, ldat, scales,
+    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, m, wts, At, out_t, ldat, scales,
                                         fp8_scale_ld(m), block_mask, st, m);
 }
 
@@ -596,26 +655,31 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
                         l >= kStrip;
     if (direct) {
         const int64_t lf = l / kStrip * kStrip;
-        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, row_scale, BtT, out_t, ldbt, scales,
+        // the workspace holds the remainder's strips (if any) and the entry weights
+        if ((lf < l || row_scale) && (!ws || ws_bytes < sketch_workspace_bytes(p, l - lf, b_t)))
+            return OS_ERR_WORKSPACE;
+        const float *wts = nullptr;
+        if (row_scale) OSK_TRY(make_weights(p, row_scale, block_mask, ws_weights(p, ws, l - lf, b_t), &wts, st));
+        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, wts, BtT, out_t, ldbt, scales,
                                      fp8_scale_ld(l), block_mask, st, l));
         if (lf == l) return OS_OK;
-        if (!ws || ws_bytes < sketch_workspace_bytes(p, l - lf, b_t)) return OS_ERR_WORKSPACE;
         float *Xs = (float *)ws_base(ws);
         OSK_TRY(launch_pack_rows<float>((const float *)B + lf, ldb, p->n, l - lf, Xs, st));
         char *yt = (char *)BtT + (size_t)lf * ldbt * dtype_size(out_t);
         float *sc = scales ? scales + lf : nullptr;   // slice-major: the remainder's rows start at lf
-        return launch_gather<float>(p, Xs, l - lf, row_scale, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask, st,
-                                    l);
+        return launch_gather<float>(p, Xs, l - lf, wts, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask, st, l);
     }
     if (!ws || ws_bytes < sketch_workspace_bytes(p, l, b_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);
+    const float *wts = nullptr;
+    OSK_TRY(make_weights(p, row_scale, block_mask, ws_weights(p, ws, l, b_t), &wts, st));
     if (b_t == OS_F32) {
         OSK_TRY(launch_pack_rows<float>((const float *)B, ldb, p->n, l, (float *)Xs, st));
-        return launch_gather<float>(p, (const float *)Xs, l, row_scale, BtT, out_t, ldbt, scales, fp8_scale_ld(l),
+        return launch_gather<float>(p, (const float *)Xs, l, wts, BtT, out_t, ldbt, scales, fp8_scale_ld(l),
                                     block_mask, st, l);
     }
     OSK_TRY(launch_pack_rows<__nv_bfloat16>((const __nv_bfloat16 *)B, ldb, p->n, l, (__nv_bfloat16 *)Xs, st));
-    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, l, row_scale, BtT, out_t, ldbt, scales,
+    return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, l, wts, BtT, out_t, ldbt, scales,
                                         fp8_scale_ld(l), block_mask, st, l);
 }
 
