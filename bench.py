@@ -394,41 +394,42 @@ def run_ours(args):
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
             "algorithmic_per_launch": per_launch}
 
-    # ---- errors (not timed): sampled rows/cols against the FP64 oracle ----
+    # ---- the cpu_baseline leg (not timed on the GPU): the FP64 oracle on a
+    # bounded sample, and sampled entries of C set beside the oracle's ----
     err = None
     cpu = None
-    if rank == 0 and not args.no_check:
+    if _cpu_leg(args, rank, world):
         import oracle
-        rows = sorted({0, 1, 2, 777 % w.m, w.m // 4, w.m // 2, (3 * w.m) // 4, w.m - 1})
-        cols = sorted({0, 3, 4096 % w.l, 5000 % w.l, w.l // 3, (2 * w.l) // 3, w.l - 2, w.l - 1})
-        h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
-        Ar = w.left_rows(rows).astype(np.float64)
-        Bc = np.ascontiguousarray(w.right_cols(cols).T, dtype=np.float64)
-        At_r = oracle.sketch_left(Ar, h, s, w.b)
-        Bt_c = oracle.sketch_right(Bc, h, s, w.b)
-        if gd == "bf16":
-            C_or = oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(Bt_c), w.b, w.mask)
-        elif gd == "fp8":
-            Aq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(At_r))
-            Bq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(Bt_c.T)).T
-            C_or = oracle.masked_product(Aq, Bq, w.b, w.mask)
-        else:
-            C_or = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
-        C_or_exact_sketch = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
-        ops.matmul(p, A, B, w.mask, gd, C=C, workspace=ws_mm)
-        C_s = C[rows][:, cols].cpu().numpy().astype(np.float64)
-        AB = Ar @ Bc
-        if exact is not None:
-            exact["vs_exact_rel_frob"] = oracle.rel_frob(exact_C[rows][:, cols].cpu().numpy(), Ar @ Bc)
-        err = {"vs_oracle_rel_frob": oracle.rel_frob(C_s, C_or),
-               "vs_exact_rel_frob": oracle.rel_frob(C_s, AB),
-               "oracle_sketch_vs_exact_rel_frob": oracle.rel_frob(C_or_exact_sketch, AB),
-               "sample": f"{len(rows)}x{len(cols)} entries of C; oracle emulates {gd} operand rounding"}
-        if not args.no_cpu_baseline:
-            rs = args.ref_sample or calibrated_sample(w, 10.0)
-            t_cpu, threads, desc = oracle_sample_time(w, rs, rs)
-            cpu = {"value": 2.0 * rs * w.n * rs / t_cpu / 1e12, "unit": UNIT,
-                   "cores": threads, "kind": "oracle", "sample": desc}
+        if not args.no_check:
+            rows = sorted({0, 1, 2, 777 % w.m, w.m // 4, w.m // 2, (3 * w.m) // 4, w.m - 1})
+            cols = sorted({0, 3, 4096 % w.l, 5000 % w.l, w.l // 3, (2 * w.l) // 3, w.l - 2, w.l - 1})
+            h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+            Ar = w.left_rows(rows).astype(np.float64)
+            Bc = np.ascontiguousarray(w.right_cols(cols).T, dtype=np.float64)
+            At_r = oracle.sketch_left(Ar, h, s, w.b)
+            Bt_c = oracle.sketch_right(Bc, h, s, w.b)
+            if gd == "bf16":
+                C_or = oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(Bt_c), w.b, w.mask)
+            elif gd == "fp8":
+                Aq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(At_r))
+                Bq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(Bt_c.T)).T
+                C_or = oracle.masked_product(Aq, Bq, w.b, w.mask)
+            else:
+                C_or = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
+            C_or_exact_sketch = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
+            ops.matmul(p, A, B, w.mask, gd, C=C, workspace=ws_mm)
+            C_s = C[rows][:, cols].cpu().numpy().astype(np.float64)
+            AB = Ar @ Bc
+            if exact is not None:
+                exact["vs_exact_rel_frob"] = oracle.rel_frob(exact_C[rows][:, cols].cpu().numpy(), Ar @ Bc)
+            err = {"vs_oracle_rel_frob": oracle.rel_frob(C_s, C_or),
+                   "vs_exact_rel_frob": oracle.rel_frob(C_s, AB),
+                   "oracle_sketch_vs_exact_rel_frob": oracle.rel_frob(C_or_exact_sketch, AB),
+                   "sample": f"{len(rows)}x{len(cols)} entries of C; oracle emulates {gd} operand rounding"}
+        rs = args.ref_sample or calibrated_sample(w, 10.0)
+        t_cpu, threads, desc = oracle_sample_time(w, rs, rs)
+        cpu = {"value": 2.0 * rs * w.n * rs / t_cpu / 1e12, "unit": UNIT,
+               "cores": threads, "kind": "oracle", "sample": desc}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -482,6 +483,14 @@ def _time_phases(phases, steps, warmup, world):
     return total / steps, per, clk
 
 
+def _cpu_leg(args, rank: int, world: int) -> bool:
+    """The cpu_baseline leg: rank 0 of a one-GPU run, unless --no-cpu-baseline.
+    It is the one place outside --impl reference where bench.py runs the FP64
+    oracle: timed on a bounded sample of the workload (cpu_baseline), and, unless
+    --no-check, its outputs on that sample set beside the GPU's (error)."""
+    return rank == 0 and world == 1 and not args.no_cpu_baseline
+
+
 def _init_dist():
     """One process per GPU (torchrun's RANK / LOCAL_RANK / WORLD_SIZE, rendezvous at
     MASTER_ADDR); a single process needs no process group."""
@@ -517,7 +526,6 @@ def run_hessian(args):
     """H = A D A^T (Sec. 5.2's normal matrix): left sketch with col_scale = sqrt(D),
     then the symmetric masked product (B~ = A~), BF16 operands."""
     import torch
-    import oracle
     from paper_1811_02653_gb300 import build, ops
     from paper_1811_02653_gb300 import workloads as W
     world, rank, _ = _init_dist()
@@ -560,25 +568,26 @@ def run_hessian(args):
     gemm = {"tflops": gemm_flop / (t_g * 1e-3) / 1e12,
             "frac_of_sustained_bf16": gemm_flop / (t_g * 1e-3) / 1e12 / peaks.get("bf16_tflops_sustained", 1710.4)}
     err, cpu = None, None
-    if rank == 0 and not args.no_check:
+    if _cpu_leg(args, rank, world):
+        import oracle
         rows = [0, 1, 777, 2048, 3333, 4095]
         A_r = A[rows].cpu().numpy().astype(np.float64)
         h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
-        At_r = oracle.sketch_left(A_r, h, s, w.b, cs_h.astype(np.float64))
-        H_or = oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(At_r).T, w.b, w.mask)
-        H_ex = (A_r * cs_h.astype(np.float64) ** 2) @ A_r.T
-        H_s = H[rows][:, rows].cpu().numpy().astype(np.float64)
-        err = {"vs_oracle_rel_frob": oracle.rel_frob(H_s, H_or), "vs_exact_rel_frob": oracle.rel_frob(H_s, H_ex),
-               "sample": f"{len(rows)}x{len(rows)} entries of H; oracle emulates bf16 operand rounding"}
-        if not args.no_cpu_baseline:
-            nr = 2
-            t0 = time.perf_counter()
-            At_c = oracle.sketch_left(A_r[:nr], h, s, w.b, cs_h.astype(np.float64))
-            oracle.masked_product(At_c, At_c.T, w.b, w.mask)
-            t_cpu = time.perf_counter() - t0
-            cpu = {"value": 2.0 * nr * w.n * nr / t_cpu / 1e12, "unit": UNIT,
-                   "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
-                   "sample": f"{nr} rows of A at full n={w.n} with sqrt(D): sketch and the {nr}x{nr} block of H in FP64"}
+        if not args.no_check:
+            At_r = oracle.sketch_left(A_r, h, s, w.b, cs_h.astype(np.float64))
+            H_or = oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(At_r).T, w.b, w.mask)
+            H_ex = (A_r * cs_h.astype(np.float64) ** 2) @ A_r.T
+            H_s = H[rows][:, rows].cpu().numpy().astype(np.float64)
+            err = {"vs_oracle_rel_frob": oracle.rel_frob(H_s, H_or), "vs_exact_rel_frob": oracle.rel_frob(H_s, H_ex),
+                   "sample": f"{len(rows)}x{len(rows)} entries of H; oracle emulates bf16 operand rounding"}
+        nr = 2
+        t0 = time.perf_counter()
+        At_c = oracle.sketch_left(A_r[:nr], h, s, w.b, cs_h.astype(np.float64))
+        oracle.masked_product(At_c, At_c.T, w.b, w.mask)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": 2.0 * nr * w.n * nr / t_cpu / 1e12, "unit": UNIT,
+               "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+               "sample": f"{nr} rows of A at full n={w.n} with sqrt(D): sketch and the {nr}x{nr} block of H in FP64"}
     cfg = {"workload": w.name, "m": w.m, "n": w.n, "l": w.m, "b": w.b, "N": w.N, "e": w.e,
            "kept_blocks": [j for j in range(w.P) if (w.mask >> j) & 1], "gemm_dtype": "bf16",
            "input_dtype": "f32", "l2": "inputs (17.2 GB) larger than L2; no flush needed",
@@ -594,7 +603,6 @@ def run_batched(args):
     """256 uneven products in one CUDA graph (parallel sketch branches, one
     grouped persistent tcgen05 GEMM), autotuned."""
     import torch
-    import oracle
     from paper_1811_02653_gb300 import build, ops
     from paper_1811_02653_gb300 import workloads as W
     world, rank, _ = _init_dist()
@@ -619,27 +627,37 @@ def run_batched(args):
                      "whole graph (pack_cols, sketch_gather, gemm_grouped): sketch bytes / run time")
     gemm_flop = float(sum(2 * m * 4 * (n // 32) * l for m, n, l in shapes))
     err = None
-    if rank == 0 and not args.no_check:
+    cpu = None
+    if _cpu_leg(args, rank, world):
+        import oracle
         sample = [0, 100, 255, max(range(256), key=lambda q: shapes[q][1])]
-        worst = 0.0
+        worst, t_cpu, flop = 0.0, 0.0, 0.0
         for q in sample:
             A, B, C, p, mask = dev[q]
             m, n, l = shapes[q]
             rows, cols = sorted({0, m // 2, m - 1}), sorted({0, l // 3, l - 1})
             A_r = A[rows].cpu().numpy().astype(np.float64)
             B_c = B[:, cols].cpu().numpy().astype(np.float64)
+            t0 = time.perf_counter()
             h, s = oracle.hash_tables(n, n // 32, 4, 1, 0)
             ref = oracle.masked_product(oracle.round_bf16(oracle.sketch_left(A_r, h, s, n // 32)),
                                         oracle.round_bf16(oracle.sketch_right(B_c, h, s, n // 32)), n // 32, mask)
+            t_cpu += time.perf_counter() - t0
+            flop += 2.0 * len(rows) * n * len(cols)
             worst = max(worst, oracle.rel_frob(C[rows][:, cols].cpu().numpy().astype(np.float64), ref))
-        err = {"vs_oracle_rel_frob_max": worst,
-               "sample": f"3x3 entries of C in products {sample}; oracle emulates bf16 operand rounding"}
+        if not args.no_check:
+            err = {"vs_oracle_rel_frob_max": worst,
+                   "sample": f"3x3 entries of C in products {sample}; oracle emulates bf16 operand rounding"}
+        cpu = {"value": flop / t_cpu / 1e12, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS",
+                                                                                      os.cpu_count() or 1)),
+               "kind": "oracle", "sample": f"3x3 entries of C in products {sample}, hash tables, both "
+                                           f"sketches and the masked product in FP64 (effective flop 2*3*n*3)"}
     cfg = {"workload": "batched: 256 uneven products, m,l ~ U[256,4096], n log-U[8192,131072], b=n/32, N=4, e=1, "
                        "product p drops block p mod 5", "count": 256,
            "input_bytes": sum((m + l) * n * 4 for m, n, l in shapes), "gemm_dtype": "bf16", "input_dtype": "f32",
            "l2": "inputs (182 GB) larger than L2; no flush needed", "parallelism": f"replicas{world}",
            "graph": {k_: v_ for k_, v_ in info.items()}, "create_s": round(t_create, 2)}
-    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, None, None,
+    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, cpu, None,
                  info["kernel_launches"] * args.steps, clk, err, world,
                  gemm={"flop_per_run": gemm_flop})
     if rank == 0:
@@ -651,7 +669,6 @@ def run_batched(args):
 def run_autograd(args):
     """Forward C = (X S)(S^T G)/k and backward dX, dG through the autograd Function."""
     import torch
-    import oracle
     from paper_1811_02653_gb300 import build, ops
     from paper_1811_02653_gb300 import autograd as AG
     from paper_1811_02653_gb300 import workloads as W
@@ -679,23 +696,31 @@ def run_autograd(args):
     t_f = per["forward"]
     fwd_bytes = (w.m * w.n + w.n * w.l) * 2 + (w.m + w.l) * w.k * w.b * 2 + w.m * w.l * 4
     roof = _hbm_roof(peaks, peak_kind, fwd_bytes, t_f, "forward: left + right sketch + masked GEMM")
-    err = None
-    if rank == 0 and not args.no_check:
+    err, cpu = None, None
+    if _cpu_leg(args, rank, world):
+        import oracle
         rows, cols = [0, 2048, 4095], [0, 1024, 4095]
-        h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
         X_r = X.detach()[rows].float().cpu().numpy().astype(np.float64)
         G_c = G.detach()[:, cols].float().cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
         ref = oracle.masked_product(oracle.round_bf16(oracle.sketch_left(X_r, h, s, w.b)),
                                     oracle.round_bf16(oracle.sketch_right(G_c, h, s, w.b)), w.b, w.mask)
-        err = {"forward_vs_oracle_rel_frob": oracle.rel_frob(
-            state["C"].detach()[rows][:, cols].cpu().numpy().astype(np.float64), ref),
-            "sample": "3x3 entries of C (gradients: tests/test_gpu_autograd.py)"}
+        t_cpu = time.perf_counter() - t0
+        if not args.no_check:
+            err = {"forward_vs_oracle_rel_frob": oracle.rel_frob(
+                state["C"].detach()[rows][:, cols].cpu().numpy().astype(np.float64), ref),
+                "sample": "3x3 entries of C (gradients: tests/test_gpu_autograd.py)"}
+        cpu = {"value": 2.0 * len(rows) * w.n * len(cols) / t_cpu / 1e12, "unit": UNIT,
+               "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+               "sample": "3x3 entries of the forward product at full n: hash tables, both sketches and the "
+                         "masked product in FP64 (effective flop 2*3*n*3)"}
     cfg = {"workload": w.name, "m": w.m, "n": w.n, "l": w.l, "b": w.b, "N": w.N, "e": w.e,
            "kept_blocks": [j for j in range(w.P) if (w.mask >> j) & 1], "gemm_dtype": "bf16",
            "input_dtype": "bf16", "recompute": bool(args.recompute),
            "metric_note": "effective flop = 6mnl (forward + dX + dG as exact GEMMs)",
            "l2": "inputs (1.07 GB) larger than L2; no flush needed", "parallelism": f"replicas{world}"}
-    line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, None, None, None, clk, err, world)
+    line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, cpu, None, None, clk, err, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -782,6 +807,96 @@ def run_lp(args):
     return 0
 
 
+def run_sec51(args):
+    """Sec. 5.1's matrix A(x, y) = x + y with B = A^T at the paper's sizes
+    (b = 2048, m = l = 10b, n = 60b, sketch dimension z = 30b), e sketch blocks
+    ignored per b x b block of C.  The timed step is one product at e = 4 (both
+    sketches and the per-block masked GEMM); the mean relative error over ten
+    sketch seeds is reported for e = 0 .. 10."""
+    import torch
+    from paper_1811_02653_gb300 import build, ops
+    from paper_1811_02653_gb300 import workloads as W
+    world, rank, _ = _init_dist()
+    build.build()
+    peaks, peak_kind = _peaks()
+    blk, P = 2048, 30
+    m = l = 10 * blk
+    n = 60 * blk
+    nb = m // blk
+    A, B, AB = W.sec51_device(m, n, "cuda")
+    ws = torch.empty(ops.sketch_workspace(ops.plan(n, blk, P - 4, 4, 0), m), dtype=torch.uint8, device="cuda")
+    wsr = torch.empty(ops.sketch_workspace(ops.plan(n, blk, P - 4, 4, 0), 0), dtype=torch.uint8, device="cuda")
+    state = {}
+
+    def sketches(seed):
+        p = ops.plan(n, blk, P - 4, 4, seed)
+        state["p"] = p
+        state["At"], _ = ops.sketch_left(p, A, "bf16", out=state.get("At"), workspace=ws)
+        state["Bt"], _ = ops.sketch_right(p, B, "bf16", out=state.get("Bt"), workspace=wsr)
+
+    ab2 = float(ops.frob(AB, AB)[1])
+    rel = {e: [] for e in range(11)}
+    for seed in range(10):
+        sketches(seed)
+        for e in range(11):
+            masks = torch.from_numpy(W.straggler_block_masks(P, e, nb, nb, seed, 0)).cuda()
+            state["C"] = ops.gemm_masked_blocks(state["p"], state["At"], state["Bt"], masks, blk, blk,
+                                                C=state.get("C"))
+            rel[e].append(math.sqrt(float(ops.frob(state["C"], AB)[0]) / ab2))
+    masks4 = torch.from_numpy(W.straggler_block_masks(P, 4, nb, nb, 0, 0)).cuda()
+    sketches(0)
+    p = state["p"]
+
+    def left():
+        ops.sketch_left(p, A, "bf16", out=state["At"], workspace=ws)
+
+    def right():
+        ops.sketch_right(p, B, "bf16", out=state["Bt"], workspace=wsr)
+
+    def gemm():
+        ops.gemm_masked_blocks(p, state["At"], state["Bt"], masks4, blk, blk, C=state["C"])
+
+    ms, per, clk = _time_phases([("sketch_left (pack + gather)", left), ("sketch_right (gather in place)", right),
+                                 ("gemm_masked_blocks", gemm)], args.steps, args.warmup, world)
+    value = _job_value(2.0 * m * n * l, ms, world)
+    flop = 2.0 * m * (P - 4) * blk * l
+    ach = flop / (per["gemm_masked_blocks"] * 1e-3) / 1e12
+    pk = peaks.get("bf16_tflops")
+    roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk if pk else None,
+            "traffic": None, "kernel": "gemm_pair_bf16_kernel (BF16, cta_group::2, per-block masks)",
+            "peak_source": f"bf16_tflops burst, {peak_kind} (MEASURED_PEAKS.json)",
+            "algorithmic_per_launch": {"flop": flop, "note": "2 m k b l, k = 26 kept blocks per block of C"}}
+    err = {"mean_rel_frob_by_e": {e: statistics.mean(v) for e, v in rel.items()},
+           "max_rel_frob_by_e": {e: max(v) for e, v in rel.items()},
+           "instances": 10, "paper_context": "Fig. 5b: 0.8 % average error with 4 of 30 workers ignored"}
+    cpu = None
+    if _cpu_leg(args, rank, world):
+        import oracle
+        U, V = W.sec51_factors(m, n)
+        err["expected_rms_rel_by_e"] = {e: math.sqrt(oracle.expected_sq_error_factored(U, V, V, U, P - e, blk)
+                                                     / ab2) for e in range(11)}
+        rows = [0, m // 2, m - 1]
+        A_r = A[rows].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        h, s = oracle.hash_tables(n, blk, P - 4, 4, 0)
+        At_r = oracle.sketch_left(A_r, h, s, blk)
+        oracle.masked_product(At_r, np.ascontiguousarray(At_r.T), blk, (1 << P) - 1 - 0b1111)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": 2.0 * len(rows) * n * len(rows) / t_cpu / 1e12, "unit": UNIT,
+               "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+               "sample": "3 rows of A (B = A^T: the same 3 columns of B) at full n: hash tables, sketch and the "
+                         "3x3 masked product in FP64 (effective flop 2*3*n*3)"}
+    cfg = {"workload": f"sec 5.1: A(x,y) = x+y {m}x{n}, B = A^T; b={blk}, P={P} (z = 30b); "
+                       f"4 of 30 blocks ignored per {blk}x{blk} block of C",
+           "m": m, "n": n, "l": l, "b": blk, "P": P, "e_per_block": 4, "gemm_dtype": "bf16", "input_dtype": "f32",
+           "l2": "A and B (10 GB each) larger than L2; no flush needed", "parallelism": f"replicas{world}"}
+    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, cpu, None, 3 * args.steps, clk, err,
+                 world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -794,7 +909,7 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-GEMM comparison")
-    ap.add_argument("--workload", default="square", choices=["square", "hessian", "batched", "autograd", "lp"],
+    ap.add_argument("--workload", default="square", choices=["square", "hessian", "batched", "autograd", "lp", "sec51"],
                     help="square (default: the headline line), or another workload of the suite")
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
     ap.add_argument("--recompute", action="store_true", help="autograd: recompute the sketches in backward")
@@ -812,6 +927,8 @@ def main():
         return run_autograd(args)
     if args.workload == "lp":
         return run_lp(args)
+    if args.workload == "sec51":
+        return run_sec51(args)
     return run_ours(args)
 
 

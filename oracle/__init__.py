@@ -328,6 +328,23 @@ def expected_sq_error(A, B, k: int, b: int) -> float:
     return total / (k * b)
 
 
+def expected_sq_error_factored(U, V, Y, W, k: int, b: int) -> float:
+    """expected_sq_error for factored operands A = U V^T (m x n) and B = Y W^T
+    (n x l), without forming them: every term of the closed form is a trace of
+    small Gram matrices, and the column norms ||A[:,i]||^2 = v_i^T (U^T U) v_i,
+    row norms ||B[i,:]||^2 = y_i^T (W^T W) y_i (Sec. 5.1's rank-2 matrix
+    A(x, y) = x + y at full size)."""
+    U, V, Y, W = (np.asarray(t, np.float64) for t in (U, V, Y, W))
+    Gu, Gv, Gy, Gw = U.T @ U, V.T @ V, Y.T @ Y, W.T @ W
+    A2 = np.trace(Gu @ Gv)
+    B2 = np.trace(Gy @ Gw)
+    M = V.T @ Y                                    # AB = U M W^T
+    AB2 = np.trace(M.T @ Gu @ M @ Gw)
+    a2 = np.einsum("ij,jk,ik->i", V, Gu, V)
+    b2 = np.einsum("ij,jk,ik->i", Y, Gw, Y)
+    return (A2 * B2 + AB2 - 2.0 * (a2 * b2).sum()) / (k * b)
+
+
 def rel_frob(x, ref) -> float:
     x = np.asarray(x, np.float64)
     ref = np.asarray(ref, np.float64)

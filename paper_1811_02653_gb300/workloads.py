@@ -297,3 +297,25 @@ def straggler_block_masks(P: int, e: int, rows: int, cols: int, seed: int, it: i
     if shared:
         out[:] = out[0, 0]
     return out
+
+
+def sec51_factors(m: int, n: int):
+    """Factors of Sec. 5.1's matrix A(x, y) = x + y (x = 1..m, y = 1..n):
+    A = U V^T with U = [x, 1] (m x 2) and V = [1, y] (n x 2); B = A^T = V U^T."""
+    x = np.arange(1, m + 1, dtype=np.float64)
+    y = np.arange(1, n + 1, dtype=np.float64)
+    return np.stack([x, np.ones(m)], 1), np.stack([np.ones(n), y], 1)
+
+
+def sec51_device(m: int, n: int, device):
+    """A(x, y) = x + y (m x n, FP32, exact below 2^24) and B = A^T (n x m), both
+    row-major on a CUDA device, and the exact product A A^T rounded once to
+    FP32 from FP64: (A A^T)[x, x'] = n x x' + (x + x') sum(y) + sum(y^2)."""
+    import torch
+    x = torch.arange(1, m + 1, dtype=torch.float64, device=device)
+    y = torch.arange(1, n + 1, dtype=torch.float64, device=device)
+    A = x.float()[:, None] + y.float()[None, :]          # integers below 2^24: exact in FP32
+    B = A.t().contiguous()
+    sy, syy = float(n * (n + 1) / 2), float(n * (n + 1) * (2 * n + 1) / 6)
+    AB = (n * x[:, None] * x[None, :] + (x[:, None] + x[None, :]) * sy + syy).float()
+    return A, B, AB

@@ -410,3 +410,41 @@ def test_masked_product_blocks_brute_force():
             k = bin(masks[i][j]).count("1")
             ref = A[rs] @ (Ssel @ Ssel.T / k) @ B[:, cs]
             assert np.allclose(C[rs, cs], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_expected_error_factored_equals_the_dense_form():
+    # the factored closed form is the same number as the dense one: random
+    # factors, and Sec. 5.1's rank-2 matrix A(x, y) = x + y with B = A^T
+    rng = _rng(21)
+    U, V = rng.standard_normal((6, 2)), rng.standard_normal((96, 2))
+    Y, W = rng.standard_normal((96, 3)), rng.standard_normal((5, 3))
+    dense = oracle.expected_sq_error(U @ V.T, Y @ W.T, 4, 8)
+    assert abs(oracle.expected_sq_error_factored(U, V, Y, W, 4, 8) - dense) <= 1e-10 * dense
+    m, n = 40, 240
+    x, y = np.arange(1, m + 1.0), np.arange(1, n + 1.0)
+    A = x[:, None] + y[None, :]
+    Uf, Vf = np.stack([x, np.ones(m)], 1), np.stack([np.ones(n), y], 1)
+    dense = oracle.expected_sq_error(A, A.T, 26, 16)
+    assert abs(oracle.expected_sq_error_factored(Uf, Vf, Vf, Uf, 26, 16) - dense) <= 1e-10 * dense
+
+
+def test_per_block_kept_sets_keep_the_expected_error():
+    # Alg. 3's rule per block of C: every block keeps k of its own P sketch
+    # blocks; each entry's variance is still (1/k) times one block's, so the
+    # expected squared error is the same closed form (Monte Carlo over seeds)
+    rng = _rng(22)
+    m, n, l, b, N, e = 8, 96, 8, 8, 4, 1
+    P = N + e
+    A = rng.standard_normal((m, n))
+    B = rng.standard_normal((n, l)) + 0.5 * A.T
+    AB = A @ B
+    errs = []
+    for seed in range(2000):
+        h, s = oracle.hash_tables(n, b, N, e, 90_000 + seed)
+        masks = [[((1 << P) - 1) & ~(1 << int(t)) for t in rng.integers(0, P, size=2)] for _ in range(2)]
+        C = oracle.masked_product_blocks(oracle.sketch_left(A, h, s, b), oracle.sketch_right(B, h, s, b),
+                                         b, masks, 4, 4)
+        errs.append(((C - AB) ** 2).sum())
+    errs = np.array(errs)
+    expect = oracle.expected_sq_error(A, B, N, b)
+    assert abs(errs.mean() - expect) < 5 * errs.std() / np.sqrt(len(errs))
