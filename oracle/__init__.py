@@ -22,11 +22,17 @@ Every function cites the passage it follows:
                         to every block of C on its own (its own kept set).
 * ``gradients``      -- the adjoint of the bilinear map C(X, G) of Eq. 3.
 * ``expected_sq_error`` -- Lemma "countEV" (appendix B) exact variance, summed
-                        over the entries of C as in Lemma "lemma2".
+                        over the entries of C as in Lemma "lemma2";
+                        ``expected_sq_error_factored`` the same closed form
+                        for factored operands (Sec. 5.1's rank-2 matrix).
+* ``oracle.lp``      -- the log-barrier interior-point LP of Sec. 5.2 with the
+                        exact Hessian.
 
-Readings where the paper is silent (hash family, 0-based buckets, the 1/k
-scale, quantiser rules) are listed in the design doc.  No value here ever comes
-from the CUDA path.
+Where the paper is silent this module takes these readings: the hash family
+is splitmix64 (seeded per block, then per index), buckets are 0-based, the
+product is scaled by 1/k for k kept blocks, and the BF16/FP8 quantisers round
+to nearest even (FP8 with a power-of-two scale per 128 sketched columns).  No
+value here ever comes from the CUDA path.
 """
 from __future__ import annotations
 

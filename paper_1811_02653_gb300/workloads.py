@@ -11,7 +11,7 @@ that their inner products are exact in FP64 in any summation order; every
 matrix is formed in FP64 and rounded once to FP32.
 
 Workloads (sizes of the paper's experiments are context; these are the
-synthetic stand-ins, see the design doc for the recipe):
+synthetic stand-ins):
 
 * ``small``   -- A 512x4096, B 4096x512, N(0,1); b=256, N=4, e=1; block 2
                  dropped (0-based); hash seed 0.
