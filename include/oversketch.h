@@ -323,7 +323,11 @@ OS_API os_status oversketch_matmul_host(oversketch_plan_t plan, const void *A, o
  *   unsketch_rows: dG[i, c] = scale * sum_t sigma_j(i) U[t*b + h_j(i), c],  j = kept[t]
  *                  U: (k*b) x l FP32 (ldu); dG: n x l in dtype g_t (ldg).
  * x_t / g_t: OS_F32 or OS_BF16.  Sums in FP32 over kept blocks in ascending
- * order.  Errors: OS_ERR_MASK, OS_ERR_INVALID_ARG, OS_ERR_DTYPE, OS_ERR_CUDA.
+ * order.  unsketch_cols stages up to four rows of T per CTA in shared memory
+ * when a row (4*k*b bytes) fits in 200 KB; longer rows are read from global
+ * memory and then m <= 65535 (else OS_ERR_UNSUPPORTED).
+ * Errors: OS_ERR_MASK, OS_ERR_INVALID_ARG, OS_ERR_DTYPE, OS_ERR_UNSUPPORTED,
+ * OS_ERR_CUDA.
  */
 OS_API os_status oversketch_unsketch_cols(oversketch_plan_t plan, const float *T, int64_t m, int64_t ldt,
                                    uint64_t mask, float scale, void *dX, os_dtype x_t,

@@ -395,6 +395,51 @@ __global__ void __launch_bounds__(256) unsketch_cols_kernel(
     }
 }
 
+// The same sums with the CTA's R rows of T staged in shared memory: a CTA owns
+// rows r0 .. r0+R-1 of dX and sweeps all n columns, so each table entry h_j(i)
+// is read once for R rows and the k random reads per output hit shared memory
+// instead of a 32-byte L2 sector each.  Same order of operations as above, so
+// the results are bitwise equal.
+template <typename OutT, int R>
+__global__ void __launch_bounds__(256) unsketch_cols_smem_kernel(
+    const float *__restrict__ T, int64_t m, int64_t ldt, int64_t kb, const uint32_t *__restrict__ hs, int64_t n,
+    int32_t b, BlockList kept, float scale, OutT *__restrict__ dX, int64_t ldx) {
+    extern __shared__ float4 ts4[];
+    float *ts = reinterpret_cast<float *>(ts4);     // [R][kb]
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    const int rows = (int)(m - r0 < R ? m - r0 : R);
+    for (int r = 0; r < rows; ++r) {
+        const float *src = T + (r0 + r) * ldt;
+        for (int64_t c = threadIdx.x; c < kb; c += blockDim.x) ts[r * kb + c] = __ldg(src + c);
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        float acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0.f;
+        for (int t = 0; t < kept.count; ++t) {
+            const uint32_t v = __ldg(hs + (int64_t)kept.idx[t] * n + i);
+            const int64_t c = (int64_t)t * b + (v & kIndexMask);   // kept blocks compacted
+            const bool neg = (v & kSignBit) != 0u;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float x = ts[r * kb + c];
+                acc[r] += neg ? -x : x;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r < rows) {
+                const float y = acc[r] * scale;
+                if constexpr (sizeof(OutT) == 4)
+                    dX[(r0 + r) * ldx + i] = y;
+                else
+                    dX[(r0 + r) * ldx + i] = __float2bfloat16_rn(y);
+            }
+        }
+    }
+}
+
 // dG[i, c] = scale * sum_{t < k} sigma_j(i) U[t*b + h_j(i), c], j = kept[t] (U holds
 // the kept blocks only); one warp per row i, whole-row gathers of U.
 template <typename OutT>
@@ -691,8 +736,33 @@ os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t l
     if (ldt < (int64_t)kcnt * p->b || ldx < p->n) return OS_ERR_INVALID_ARG;
     if (x_t != OS_F32 && x_t != OS_BF16) return OS_ERR_DTYPE;
     if (m == 0) return OS_OK;
-    if (m > 65535) return OS_ERR_UNSUPPORTED;
     const BlockList kept = mask_to_list(mask, p->P);
+    // rows of T staged per CTA: the most that keep two or more CTAs per SM (up to
+    // 96 KB each), else one row in up to 200 KB, else the unstaged kernel
+    const int64_t kb = (int64_t)kcnt * p->b;
+    const size_t row_bytes = (size_t)kb * sizeof(float);
+    const int R = row_bytes * 4 <= 96 * 1024 ? 4 : row_bytes * 2 <= 96 * 1024 ? 2 : row_bytes <= 200 * 1024 ? 1 : 0;
+    if (R > 0) {
+        const size_t smem = row_bytes * R;
+        const unsigned gxs = (unsigned)((m + R - 1) / R);
+        auto launch = [&](auto kern, auto *out) -> os_status {
+            if (smem > 48 * 1024)
+                OSK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<gxs, 256, smem, st>>>(T, m, ldt, kb, p->hs, p->n, p->b, kept, scale, out, ldx);
+            return check_launch();
+        };
+        if (x_t == OS_F32) {
+            float *o = (float *)dX;
+            if (R == 4) return launch(unsketch_cols_smem_kernel<float, 4>, o);
+            if (R == 2) return launch(unsketch_cols_smem_kernel<float, 2>, o);
+            return launch(unsketch_cols_smem_kernel<float, 1>, o);
+        }
+        __nv_bfloat16 *o = (__nv_bfloat16 *)dX;
+        if (R == 4) return launch(unsketch_cols_smem_kernel<__nv_bfloat16, 4>, o);
+        if (R == 2) return launch(unsketch_cols_smem_kernel<__nv_bfloat16, 2>, o);
+        return launch(unsketch_cols_smem_kernel<__nv_bfloat16, 1>, o);
+    }
+    if (m > 65535) return OS_ERR_UNSUPPORTED;
     const int64_t gx = (p->n + 255) / 256 < 1024 ? (p->n + 255) / 256 : 1024;
     dim3 grid((unsigned)gx, (unsigned)m);
     if (x_t == OS_F32)

@@ -233,6 +233,31 @@ def test_unsketch_parity(ops):
     assert_fp32_within(dG, ref_g, bg)
 
 
+@pytest.mark.parametrize("m,n,b,N,e,mask,out", [
+    (66, 3000, 128, 4, 1, 0b10111, "f32"),      # rows of T staged 4 per CTA, last CTA partial
+    (5, 20_000, 2048, 4, 1, 0b11011, "bf16"),   # 2 per CTA (the autograd workload's k b = 8192)
+    (3, 9000, 8192, 4, 1, 0b01111, "f32"),      # one 128 KB row per CTA
+    (2, 5000, 16384, 4, 0, 0b1111, "f32"),      # rows too long to stage: the unstaged kernel
+])
+def test_unsketch_cols_staging(ops, m, n, b, N, e, mask, out):
+    rng = np.random.default_rng(m + b)
+    P = N + e
+    k = bin(mask).count("1")
+    T_sel = rng.standard_normal((m, k * b)).astype(np.float32)
+    cols = oracle.selected_columns(mask, P, b)
+    T = np.zeros((m, P * b))
+    T[:, cols] = T_sel
+    p = ops.plan(n, b, N, e, 4)
+    h, s = oracle.hash_tables(n, b, N, e, 4)
+    dX = ops.unsketch_cols(p, _dev(T_sel), mask, 0.5, out_dtype=out).float().cpu().numpy()
+    ref = oracle.unsketch_cols(T, h, s, b, mask, 0.5)
+    bound = (k + 1) * 2.0 ** -24 * oracle.unsketch_cols(np.abs(T), h, np.ones_like(s), b, mask, 0.5) + 1e-30
+    if out == "f32":
+        assert_fp32_within(dX, ref, bound)
+    else:
+        assert_bf16_within(dX, ref, bound)
+
+
 def test_frob_fp64(ops):
     rng = np.random.default_rng(15)
     X = rng.standard_normal((300, 500)).astype(np.float32)
