@@ -441,7 +441,9 @@ __global__ void __launch_bounds__(256) unsketch_cols_smem_kernel(
 }
 
 // dG[i, c] = scale * sum_{t < k} sigma_j(i) U[t*b + h_j(i), c], j = kept[t] (U holds
-// the kept blocks only); one warp per row i, whole-row gathers of U.
+// the kept blocks only); one warp per row i and 1024 columns: for each kept block
+// the warp reads the bucket's row of U with 32 independent loads per lane, and
+// the 32 sums per lane stay in registers.
 template <typename OutT>
 __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     const float *__restrict__ U, int64_t l, int64_t ldu, const uint32_t *__restrict__ hs, int64_t n,
@@ -449,22 +451,29 @@ __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 8 + warp;
     if (i >= n) return;
-    const int64_t c0 = (int64_t)blockIdx.y * 1024;
-    int64_t rows[64];
-    float sg[64];
+    const int64_t c0 = (int64_t)blockIdx.y * 1024 + lane;
+    float acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0.f;
     for (int t = 0; t < kept.count; ++t) {
-        const int j = kept.idx[t];
-        const uint32_t v = __ldg(hs + (int64_t)j * n + i);
-        rows[t] = (int64_t)t * b + (v & kIndexMask);                          // kept blocks compacted
-        sg[t] = (v & kSignBit) ? -scale : scale;
+        const uint32_t v = __ldg(hs + (int64_t)kept.idx[t] * n + i);
+        const float sg = (v & kSignBit) ? -scale : scale;
+        const float *urow = U + ((int64_t)t * b + (v & kIndexMask)) * ldu;   // kept blocks compacted
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int64_t c = c0 + 32 * q;
+            if (c < l) acc[q] = fmaf(sg, __ldg(urow + c), acc[q]);
+        }
     }
-    for (int64_t c = c0 + lane; c < min(l, c0 + 1024); c += 32) {
-        float acc = 0.f;
-        for (int t = 0; t < kept.count; ++t) acc = fmaf(sg[t], __ldg(U + rows[t] * ldu + c), acc);
-        if constexpr (sizeof(OutT) == 4)
-            dG[i * ldg + c] = acc;
-        else
-            dG[i * ldg + c] = __float2bfloat16_rn(acc);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const int64_t c = c0 + 32 * q;
+        if (c < l) {
+            if constexpr (sizeof(OutT) == 4)
+                dG[i * ldg + c] = acc[q];
+            else
+                dG[i * ldg + c] = __float2bfloat16_rn(acc[q]);
+        }
     }
 }
 
