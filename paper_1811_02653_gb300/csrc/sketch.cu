@@ -413,28 +413,47 @@ __global__ void __launch_bounds__(256) unsketch_cols_smem_kernel(
         for (int64_t c = threadIdx.x; c < kb; c += blockDim.x) ts[r * kb + c] = __ldg(src + c);
     }
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        float acc[R];
+    // four columns per thread and pass, so that four table loads per kept block
+    // are in flight at once
+    constexpr int NI = 4;
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += NI * (int64_t)blockDim.x) {
+        float acc[NI][R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = 0.f;
+        for (int u = 0; u < NI; ++u)
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[u][r] = 0.f;
         for (int t = 0; t < kept.count; ++t) {
-            const uint32_t v = __ldg(hs + (int64_t)kept.idx[t] * n + i);
-            const int64_t c = (int64_t)t * b + (v & kIndexMask);   // kept blocks compacted
-            const bool neg = (v & kSignBit) != 0u;
+            const uint32_t *hrow = hs + (int64_t)kept.idx[t] * n;
+            uint32_t v[NI];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float x = ts[r * kb + c];
-                acc[r] += neg ? -x : x;
+            for (int u = 0; u < NI; ++u) {
+                const int64_t i = i0 + (int64_t)u * blockDim.x;
+                v[u] = i < n ? __ldg(hrow + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < NI; ++u) {
+                const int64_t c = (int64_t)t * b + (v[u] & kIndexMask);   // kept blocks compacted
+                const bool neg = (v[u] & kSignBit) != 0u;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float x = ts[r * kb + c];
+                    acc[u][r] += neg ? -x : x;
+                }
             }
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (r < rows) {
-                const float y = acc[r] * scale;
-                if constexpr (sizeof(OutT) == 4)
-                    dX[(r0 + r) * ldx + i] = y;
-                else
-                    dX[(r0 + r) * ldx + i] = __float2bfloat16_rn(y);
+        for (int u = 0; u < NI; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x;
+            if (i >= n) continue;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < rows) {
+                    const float y = acc[u][r] * scale;
+                    if constexpr (sizeof(OutT) == 4)
+                        dX[(r0 + r) * ldx + i] = y;
+                    else
+                        dX[(r0 + r) * ldx + i] = __float2bfloat16_rn(y);
+                }
             }
         }
     }
@@ -455,8 +474,11 @@ __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     float acc[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) acc[q] = 0.f;
+    // the k table entries of row i, loaded at once: lane t holds kept blocks t and t + 32
+    const uint32_t v_lo = lane < kept.count ? __ldg(hs + (int64_t)kept.idx[lane] * n + i) : 0u;
+    const uint32_t v_hi = lane + 32 < kept.count ? __ldg(hs + (int64_t)kept.idx[lane + 32] * n + i) : 0u;
     for (int t = 0; t < kept.count; ++t) {
-        const uint32_t v = __ldg(hs + (int64_t)kept.idx[t] * n + i);
+        const uint32_t v = __shfl_sync(0xffffffffu, t < 32 ? v_lo : v_hi, t & 31);
         const float sg = (v & kSignBit) ? -scale : scale;
         const float *urow = U + ((int64_t)t * b + (v & kIndexMask)) * ldu;   // kept blocks compacted
 #pragma unroll
