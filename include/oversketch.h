@@ -157,8 +157,9 @@ OS_API os_status oversketch_sketch_size(double eps, double theta, int32_t b, dou
  *     Columns of blocks not listed are left untouched (the paper's remark
  *     that blocks missed while sketching become stragglers of the product).
  *   workspace: device memory of at least oversketch_sketch_workspace(plan, m,
- *     a_t) bytes; the operand is packed there strip-major (128 free indices
- *     per strip, n rows each) before the bucket gather, and with a col_scale
+ *     a_t) bytes; the operand is packed there strip-major (n rows of 512
+ *     bytes per strip: 128 FP32 or 256 BF16 free indices) before the bucket
+ *     gather, and with a col_scale
  *     the signed scales sigma_j(i) * s_i are laid out there in bucket-list
  *     order first (one coalesced load per 32 gathered rows).
  * oversketch_sketch_right:

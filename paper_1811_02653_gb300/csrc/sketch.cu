@@ -10,9 +10,9 @@
 // Right sketch: X = B (n x l), Y^T = B~^T (l x z).  Left sketch: X = A^T,
 // Y^T = A~ (m x z).
 //
-// The gather reads X in strips of 128 free indices: strip s holds
-// X[0..n-1, 128s .. 128s+127], and a random row of it is one 512-byte piece
-// (FP32).  The left operand (and a right operand whose rows are not 16-byte
+// The gather reads X in strips of W free indices (W = 128 for FP32, 256 for
+// BF16): strip s holds X[0..n-1, Ws .. Ws+W-1], and a random row of it is one
+// 512-byte piece, 16 bytes per lane of a warp.  The left operand (and a right operand whose rows are not 16-byte
 // aligned) is first packed strip-major into the workspace, n contiguous rows
 // of 128 elements per strip, zero-padded past the free extent; packing the
 // left operand is the transpose it needs anyway.  An aligned FP32 right
@@ -43,7 +43,14 @@ namespace {
 
 constexpr int kTileQ = 128;
 constexpr int kWarps = 8;
-constexpr int kStrip = 128;   // free indices per packed strip
+constexpr int kStrip = 128;   // free indices per FP32 strip (the in-place right sketch)
+
+// Free indices per packed strip of an element type: 16 bytes per lane of a warp
+// (128 FP32, 256 BF16), so every gathered row piece is 512 bytes.
+template <typename T>
+__host__ __device__ constexpr int strip_of() {
+    return 32 * (16 / (int)sizeof(T));
+}
 constexpr int kUnroll = 8;
 
 // VW consecutive elements of the free dimension per lane (strip = 32*VW).
@@ -70,6 +77,25 @@ struct Loader {
             for (int k = 0; k < VW; ++k) v[k] = to_f32(p[k]);
         }
     }
+    // 16 raw bytes (VW = 16 / sizeof(InT)) now, converted when they are summed
+    using Raw = uint4;
+    __device__ __forceinline__ static Raw load_raw(const InT *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+    __device__ __forceinline__ static void unpack(const Raw &u, float (&v)[VW]) {
+        if constexpr (std::is_same<InT, float>::value) {
+            static_assert(VW == 4, "four FP32 per 16 bytes");
+            v[0] = __uint_as_float(u.x); v[1] = __uint_as_float(u.y);
+            v[2] = __uint_as_float(u.z); v[3] = __uint_as_float(u.w);
+        } else {
+            static_assert(VW == 8, "eight BF16 per 16 bytes");
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[q]));
+                v[2 * q] = f.x;
+                v[2 * q + 1] = f.y;
+            }
+        }
+    }
     __device__ __forceinline__ static float to_f32(float x) { return x; }
     __device__ __forceinline__ static float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
     __device__ __forceinline__ static float load1(const InT *p) { return to_f32(p[0]); }
@@ -79,16 +105,17 @@ struct Loader {
 // lists point at, so the gather loop needs no predication.
 __device__ __align__(16) float g_zero_row[8];
 
-// Lane layout: lane = slot * 8 + sub.  The 4 slots of a warp gather 4
-// different members of one bucket at once (bucket lists are padded to a
-// multiple of 4), each 8-lane group reading a 32-element row segment (128 B
-// for FP32) of X; lane `sub` holds elements 4*sub .. 4*sub+3 of the strip.
+// Lane layout: lane = slot * SUBS + sub (SUBS = 32 / SLOTS lanes per member;
+// the launches use SLOTS = 1, one member per warp load).  With SLOTS > 1 the
+// slots of a warp gather different members of one bucket at once (bucket lists
+// are padded to a multiple of 4).  Lane `sub` holds the 16 bytes at elements
+// VW*sub .. VW*sub+VW-1 of the strip (VW = 4 FP32 or 8 BF16).
 // A warp owns QT/8 consecutive buckets and streams their (contiguous) padded
 // member list 32 entries at a time, keeping 8 independent 16-byte loads per
 // lane in flight and prefetching the next 32 entries.  Slot s accumulates
-// members s, s+4, s+8, ... of a bucket in ascending order and the four
-// partial sums are combined as (p0 + p1) + (p2 + p3): a fixed order, so the
-// results are bitwise reproducible.
+// members s, s+SLOTS, ... of a bucket in ascending order and the partial sums
+// are combined by a fixed butterfly (one chain when SLOTS = 1): a fixed order,
+// so the results are bitwise reproducible.
 template <typename InT, typename OutT, int QT, bool kScale, int SLOTS>
 __global__ void __launch_bounds__(kWarps * 32, 4)
 sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ldx, int64_t F,
@@ -97,7 +124,8 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                      OutT *__restrict__ Yt, int64_t ldy, float *__restrict__ scales,
                      int64_t lds, BlockList blocks, int32_t tiles_per_block, int64_t plane_elems) {
     constexpr int SUBS = 32 / SLOTS;     // lanes per member
-    constexpr int TF = 4 * SUBS;         // free indices per CTA (one strip)
+    constexpr int VW = 16 / (int)sizeof(InT);   // free indices per lane: 16 bytes
+    constexpr int TF = VW * SUBS;        // free indices per CTA (one strip)
     constexpr int PITCH = TF + 1;        // odd pitch: conflict-free column reads
     constexpr int G = 2 * SLOTS;         // groups of 4 members per batch: 8 loads per lane in flight
     constexpr int QPW = QT / kWarps;     // buckets per warp
@@ -113,7 +141,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
     const int q0 = jblk * b + (blockIdx.x - bt * tiles_per_block) * QT;
     const int qend = min(z, jblk * b + b);
     const int64_t f0 = (int64_t)blockIdx.y * TF;
-    using L = Loader<InT, 4, true>;
+    using L = Loader<InT, VW, true>;
 
     const int nb = min(QPW, qend - q0 - warp * QPW);   // buckets owned by this warp
     if (nb > 0) {
@@ -124,7 +152,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
         const uint32_t gbl = lane <= nb ? __ldg(poffs + (int64_t)jblk * (b + 1) + cb + lane) >> 2 : 0u;
         const uint32_t gend = __shfl_sync(0xffffffffu, gbl, nb);
         // row i of the strip at xbase + i * row_bytes: one wide multiply-add per member
-        const uint64_t xbase = reinterpret_cast<uint64_t>(X + blockIdx.y * strip_stride + 4 * sub);
+        const uint64_t xbase = reinterpret_cast<uint64_t>(X + blockIdx.y * strip_stride + VW * sub);
         const uint32_t row_bytes = (uint32_t)(ldx * (int64_t)sizeof(InT));
         const uint64_t zrow = reinterpret_cast<uint64_t>(g_zero_row);
 
@@ -141,10 +169,10 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
         };
         // GG groups (4*GG members) of the current bucket, entries in lanes 0 .. 4*GG-1
         // of e, their signed scales in the same lanes of w
-        auto batch = [&](auto gg, uint32_t e, float w, float (&acc)[4]) {
+        auto batch = [&](auto gg, uint32_t e, float w, float *acc) {
             constexpr int GG = decltype(gg)::value;
             constexpr int KS = 4 * GG / SLOTS;            // member loads per lane
-            float v[KS][4];
+            uint4 v[KS];
             float wgt[KS];
 #pragma unroll
             for (int k = 0; k < KS; ++k) {
@@ -156,22 +184,25 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                     wgt[k] = __uint_as_float(0x3f800000u | (ent & kSignBit));
                 }
                 const uint64_t addr = (uint64_t)(ent & kIndexMask) * row_bytes + xbase;
-                L::load(reinterpret_cast<const InT *>(ent != kPadEntry ? addr : zrow), v[k]);
+                v[k] = L::load_raw(reinterpret_cast<const InT *>(ent != kPadEntry ? addr : zrow));
             }
 #pragma unroll
-            for (int k = 0; k < KS; ++k)
+            for (int k = 0; k < KS; ++k) {
+                float x[VW];
+                L::unpack(v[k], x);
 #pragma unroll
-                for (int w = 0; w < 4; ++w) acc[w] = fmaf(wgt[k], v[k][w], acc[w]);
+                for (int w = 0; w < VW; ++w) acc[w] = fmaf(wgt[k], x[w], acc[w]);
+            }
         };
-        auto flush = [&](int t, float (&acc)[4]) {
+        auto flush = [&](int t, float *acc) {
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
+            for (int w = 0; w < VW; ++w) {
                 if constexpr (SLOTS == 4) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], 8);
                 if constexpr (SLOTS >= 2) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], 16);
             }
             if (slot == 0) {
 #pragma unroll
-                for (int w = 0; w < 4; ++w) tile[(warp * QPW + t) * PITCH + 4 * sub + w] = acc[w];
+                for (int w = 0; w < VW; ++w) tile[(warp * QPW + t) * PITCH + VW * sub + w] = acc[w];
             }
         };
 
@@ -181,7 +212,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
         uint32_t g = __shfl_sync(0xffffffffu, gbl, 0);
         uint32_t e_cur = load_entries(g);
         float w_cur = load_weights(g);
-        auto step = [&](auto gg, float (&acc)[4]) {
+        auto step = [&](auto gg, float *acc) {
             constexpr int GG = decltype(gg)::value;
             const uint32_t e_nxt = load_entries(g + GG);
             const float w_nxt = load_weights(g + GG);
@@ -192,7 +223,9 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
         };
         for (int t = 0; t < nb; ++t) {
             const uint32_t gE = __shfl_sync(0xffffffffu, gbl, t + 1);
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            float acc[VW];
+#pragma unroll
+            for (int w = 0; w < VW; ++w) acc[w] = 0.f;
             while (gE - g >= (uint32_t)G) step(std::integral_constant<int, G>(), acc);
             const uint32_t r = gE - g;   // < G
             if constexpr (G >= 8) if (r & 4u) step(std::integral_constant<int, 4>(), acc);
@@ -306,7 +339,8 @@ template <typename T, bool kVec>
 __global__ void __launch_bounds__(256) pack_rows_kernel(const T *__restrict__ X, int64_t ldx, int64_t n,
                                                         int64_t F, int64_t nstrips, T *__restrict__ Xs) {
     constexpr int V = 16 / sizeof(T);                // elements per 16-byte piece
-    constexpr int PPS = kStrip / V;                  // pieces per strip row
+    constexpr int SW = strip_of<T>();                // strip width
+    constexpr int PPS = SW / V;                      // pieces per strip row
     const int64_t pieces_per_row = nstrips * PPS;
     const int64_t total = n * pieces_per_row;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -314,7 +348,7 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(const T *__restrict__ X,
         const int64_t i = t / pieces_per_row;
         const int64_t pr = t - i * pieces_per_row;
         const int64_t s = pr / PPS, pc = pr - s * PPS;
-        const int64_t c0 = s * kStrip + pc * V;
+        const int64_t c0 = s * SW + pc * V;
         uint4 u = make_uint4(0u, 0u, 0u, 0u);
         if (kVec && c0 + V <= F) {
             u = __ldg(reinterpret_cast<const uint4 *>(X + i * ldx + c0));
@@ -323,7 +357,7 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(const T *__restrict__ X,
 #pragma unroll
             for (int k = 0; k < V; ++k) e[k] = c0 + k < F ? X[i * ldx + c0 + k] : T(0.f);
         }
-        *reinterpret_cast<uint4 *>(Xs + (s * n + i) * kStrip + pc * V) = u;
+        *reinterpret_cast<uint4 *>(Xs + (s * n + i) * SW + pc * V) = u;
     }
 }
 
@@ -338,7 +372,8 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const T *__restrict__ A,
     constexpr int V = 16 / sizeof(T);               // elements per 16-byte vector
     __shared__ T tile[32][W + 1];
     const int64_t rb = blockIdx.y;                  // 32-row block of A
-    const int64_t s = rb / (kStrip / 32), quarter = rb % (kStrip / 32);
+    constexpr int SW = strip_of<T>();               // strip width: SW / 32 row blocks per strip
+    const int64_t s = rb / (SW / 32), quarter = rb % (SW / 32);
     const int64_t i0 = (int64_t)blockIdx.x * W;
     const int tid = threadIdx.x;
     const bool whole = kVec && rb * 32 + 32 <= m && i0 + W <= n;
@@ -367,7 +402,7 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const T *__restrict__ A,
         T *e = reinterpret_cast<T *>(&u);
 #pragma unroll
         for (int k = 0; k < V; ++k) e[k] = tile[rq * V + k][c];
-        *reinterpret_cast<uint4 *>(Xs + (s * n + col) * kStrip + quarter * 32 + rq * V) = u;
+        *reinterpret_cast<uint4 *>(Xs + (s * n + col) * SW + quarter * 32 + rq * V) = u;
     }
 }
 
@@ -533,7 +568,7 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
                           const BlockList &blocks, cudaStream_t st, int64_t plane_elems = 0) {
     const int z = p->P * p->b;
     const int tpb = (p->b + QT - 1) / QT;
-    constexpr int TF = 128 / SLOTS;
+    constexpr int TF = strip_of<InT>() / SLOTS;
     dim3 grid((unsigned)(tpb * blocks.count), (unsigned)((F + TF - 1) / TF));
     if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;
     const size_t smem = sizeof(float) * QT * (TF + 1);
@@ -578,18 +613,19 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *wt
                         os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask,
                         cudaStream_t st, int64_t plane_rows = 0) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
-    const int64_t ss = p->n * kStrip;
+    constexpr int64_t W = strip_of<InT>();
+    const int64_t ss = p->n * W;
     switch (out_t) {
         case OS_F32:
-            return launch_gather_t<InT, float, kGatherQT, 1>(p, Xs, ss, kStrip, F, wts, Yt, ldy, scales, scale_ld, blocks, st);
+            return launch_gather_t<InT, float, kGatherQT, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld, blocks, st);
         case OS_BF16:
-            return launch_gather_t<InT, __nv_bfloat16, kGatherQT, 1>(p, Xs, ss, kStrip, F, wts, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<InT, __nv_bfloat16, kGatherQT, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld,
                                                               blocks, st);
         case OS_FP8E4M3:
-            return launch_gather_t<InT, __nv_fp8_e4m3, 32, 1>(p, Xs, ss, kStrip, F, wts, Yt, ldy, scales, scale_ld,
+            return launch_gather_t<InT, __nv_fp8_e4m3, 32, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld,
                                                                blocks, st);
         case OS_TF32X2:
-            return launch_gather_t<InT, Tf32Pair, kGatherQT, 1>(p, Xs, ss, kStrip, F, wts, Yt, ldy, scales, scale_ld, blocks,
+            return launch_gather_t<InT, Tf32Pair, kGatherQT, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld, blocks,
                                                          st, plane_rows * ldy);
     }
     return OS_ERR_DTYPE;
@@ -620,8 +656,9 @@ os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64
 
 template <typename T>
 os_status launch_pack_rows(const T *X, int64_t ldx, int64_t n, int64_t F, T *Xs, cudaStream_t st) {
-    const int64_t nstrips = (F + kStrip - 1) / kStrip;
-    const int64_t total = n * nstrips * (kStrip / (16 / (int64_t)sizeof(T)));
+    constexpr int64_t SW = strip_of<T>();
+    const int64_t nstrips = (F + SW - 1) / SW;
+    const int64_t total = n * nstrips * (SW / (16 / (int64_t)sizeof(T)));
     const int64_t blocks = (total + 255) / 256 < 152 * 64 ? (total + 255) / 256 : 152 * 64;
     const bool vec = aligned16(X) && (ldx * (int64_t)sizeof(T)) % 16 == 0;
     if (vec)
@@ -634,7 +671,8 @@ os_status launch_pack_rows(const T *X, int64_t ldx, int64_t n, int64_t F, T *Xs,
 template <typename T>
 os_status launch_pack_cols(const T *A, int64_t lda, int64_t m, int64_t n, T *Xs, cudaStream_t st) {
     // 32-row blocks of the (zero-padded) strips
-    dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + kStrip - 1) / kStrip * (kStrip / 32)));
+    constexpr int64_t SW = strip_of<T>();
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + SW - 1) / SW * (SW / 32)));
     if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;
     if (aligned16(A) && (lda * (int64_t)sizeof(T)) % 16 == 0)
         pack_cols_kernel<T, true><<<grid, 256, 0, st>>>(A, lda, m, n, Xs);
@@ -663,7 +701,8 @@ namespace {
 size_t ws_align(size_t x) { return (x + 255) / 256 * 256; }
 // ceil(F/128) packed strips of n x 128 elements
 size_t strip_bytes(const Plan *p, int64_t F, os_dtype in_t) {
-    return (size_t)((F + kStrip - 1) / kStrip) * kStrip * (size_t)p->n * dtype_size(in_t);
+    const int64_t sw = 32 * (16 / (int64_t)dtype_size(in_t));   // strip_of<> of the element type
+    return (size_t)((F + sw - 1) / sw) * sw * (size_t)p->n * dtype_size(in_t);
 }
 }  // namespace
 
