@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "sketched A·B effective TFLOP/s (2mnl/t) vs exact GEMM at stated Frobenius error"
 # DRAM bytes (read + write) of one gemm_pair_bf16_kernel launch on the square workload,
 # from one ncu capture of this bench (profiles/square_launch_list.md)
-TRAFFIC_GEMM_PAIR_SQUARE = 4925004800 + 1058414848
+TRAFFIC_GEMM_PAIR_SQUARE = 4875390720 + 1055008512
 UNIT = "TFLOP/s"
 
 
