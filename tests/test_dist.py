@@ -65,3 +65,27 @@ def test_single_process_needs_no_group():
     import bench
     assert bench._max_over_ranks(4.5, 1) == 4.5
     assert bench._job_value(1e12, 1.0, 1) == pytest.approx(1000.0)
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the reference arm (the FP64 oracle on the host cores) on a tiny sample of the
+    # square workload: one JSON line with the keys the measurement contract names
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        os.environ.pop(k, None)
+    out = io.StringIO()
+    args = argparse.Namespace(steps=1, warmup=0, gpus=1, ref_sample=8, shape="", dtype="bf16")
+    with contextlib.redirect_stdout(out):
+        assert bench.run_reference(args) == 0
+    lines = [l for l in out.getvalue().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"].startswith("square") and d["config"]["m"] == 16384
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
