@@ -720,7 +720,9 @@ def run_autograd(args):
            "input_dtype": "bf16", "recompute": bool(args.recompute),
            "metric_note": "effective flop = 6mnl (forward + dX + dG as exact GEMMs)",
            "l2": "inputs (1.07 GB) larger than L2; no flush needed", "parallelism": f"replicas{world}"}
-    line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, cpu, None, None, clk, err, world)
+    # per step: forward pack + gather for each operand and the masked GEMM (5); backward
+    # cast, three layout transposes, two GEMMs and two unsketch kernels (8)
+    line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, cpu, None, 13 * args.steps, clk, err, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -800,8 +802,9 @@ def run_lp(args):
            "metric_note": "effective flop = 2 m^2 n (the exact Hessian)",
            "l2": "A (839 MB FP32) larger than L2; no flush needed", "parallelism": f"replicas{world}",
            "lp_iterations": args.lp_iters, "tau": "1, doubled every 10 iterations"}
-    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, None, None, None, clk, None, world,
-                 roofline_gemm=roof_gemm, lp_runs=runs)
+    # per step: entry weights + gather (the scaled right sketch), the masked GEMM
+    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, None, None, 3 * args.steps, clk, None,
+                 world, roofline_gemm=roof_gemm, lp_runs=runs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
