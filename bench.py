@@ -543,7 +543,7 @@ def run_hessian(args):
     if args.dense_sketch:
         ws = torch.empty(ops.sketch_workspace(p, w.m), dtype=torch.uint8, device="cuda")
         At, _ = ops.sketch_left(p, A, "bf16", col_scale=cs, workspace=ws, block_mask=w.mask)
-        sk_name, sk_kernel = "sketch_left (pack + gather, col_scale)", "pack_cols_kernel + sketch_gather_kernel"
+        sk_name, sk_kernel = "sketch_left (pack + weights + gather, col_scale)", "pack_cols_kernel + entry_weights_kernel + sketch_gather_kernel"
 
         def sketch():
             ops.sketch_left(p, A, "bf16", col_scale=cs, out=At, workspace=ws, block_mask=w.mask)
@@ -593,7 +593,7 @@ def run_hessian(args):
            "input_dtype": "f32", "l2": "inputs (17.2 GB) larger than L2; no flush needed",
            "sketch": "dense gather" if args.dense_sketch else "sparse rows", "parallelism": f"replicas{world}"}
     line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, cpu,
-                 None, (3 if args.dense_sketch else 2) * args.steps, clk, err, world, gemm=gemm)
+                 None, (4 if args.dense_sketch else 2) * args.steps, clk, err, world, gemm=gemm)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
