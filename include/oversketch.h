@@ -32,6 +32,10 @@
  *   - Sketched operands are stored K-major: A~ is m x z (row r contiguous
  *     over q) and B~^T is l x z (column c of B~ contiguous over q), so both
  *     feed the tensor-core GEMM without a transpose.
+ *   - Empty outputs: when an output has no elements (m = 0 or l = 0, zero
+ *     rows to sketch or to unsketch) a call checks its other arguments and
+ *     returns OS_OK without launching anything; its data pointers may then be
+ *     NULL (empty tensors often have no storage).
  */
 #ifndef OVERSKETCH_H
 #define OVERSKETCH_H

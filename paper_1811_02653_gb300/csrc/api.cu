@@ -170,11 +170,12 @@ extern "C" os_status oversketch_gemm_masked(oversketch_plan_t plan, const void *
                                             uint64_t mask, float alpha, float beta, float *C,
                                             int64_t ldc, void *stream) {
     const Plan *p = reinterpret_cast<const Plan *>(plan);
-    if (!p || !At || !BtT || !C || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
+    if (!p || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_mask(mask, p->P));
+    if (m == 0 || l == 0) return OS_OK;   // an empty C: nothing to read or write
+    if (!At || !BtT || !C) return OS_ERR_INVALID_ARG;
     const int64_t z = (int64_t)p->P * p->b;
     if (ldat < z || ldbt < z) return OS_ERR_INVALID_ARG;
-    if (m == 0 || l == 0) return OS_OK;
     cudaStream_t st = as_stream(stream);
     switch (dt) {
         case OS_F32:
@@ -205,19 +206,19 @@ extern "C" os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os
                                        uint64_t mask, const os_opts *opts, void *workspace,
                                        size_t ws_bytes, void *stream) {
     const Plan *p = reinterpret_cast<const Plan *>(plan);
-    if (!p || !A || !C) return OS_ERR_INVALID_ARG;
+    if (!p) return OS_ERR_INVALID_ARG;
     const bool sym = opts && opts->symmetric;
     if (sym) l = m;
-    if (!sym && !B) return OS_ERR_INVALID_ARG;
     if (n != p->n || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_mask(mask, p->P));
     const os_dtype g0 = opts ? opts->gemm_dtype : OS_F32;
     if (g0 != OS_F32 && g0 != OS_BF16 && g0 != OS_FP8E4M3 && g0 != OS_TF32X2) return OS_ERR_DTYPE;
+    if (m == 0 || l == 0) return OS_OK;   // an empty C: nothing to read or write
+    if (!A || !C || (!sym && !B)) return OS_ERR_INVALID_ARG;
     const os_dtype g = sketch_dtype(p, g0);
     const MatmulLayout L = layout(p, m, l, a_t, b_t, opts);
     const size_t need = L.at_bytes + L.bt_bytes + L.as_bytes + L.bs_bytes + L.left_ws + 256;
     if (!workspace || ws_bytes < need) return OS_ERR_WORKSPACE;
-    if (m == 0 || l == 0) return OS_OK;
     cudaStream_t st = as_stream(stream);
     char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
     void *At = base;
@@ -340,20 +341,20 @@ extern "C" os_status oversketch_matmul_host(oversketch_plan_t plan, const void *
                                             int64_t m, int64_t n, int64_t l, uint64_t mask, const os_opts *opts,
                                             void *workspace, size_t ws_bytes, void *stream) {
     const Plan *p = reinterpret_cast<const Plan *>(plan);
-    if (!p || !A || !C) return OS_ERR_INVALID_ARG;
+    if (!p) return OS_ERR_INVALID_ARG;
     const bool sym = opts && opts->symmetric;
     if (sym) l = m;
-    if (!sym && !B) return OS_ERR_INVALID_ARG;
     if (n != p->n || m < 0 || l < 0 || lda < n || ldc < l || (!sym && ldb < l)) return OS_ERR_INVALID_ARG;
     if ((a_t != OS_F32 && a_t != OS_BF16) || (!sym && b_t != OS_F32 && b_t != OS_BF16)) return OS_ERR_DTYPE;
     if (sym) b_t = a_t;
     OSK_TRY(check_mask(mask, p->P));
     const os_dtype g0 = opts ? opts->gemm_dtype : OS_F32;
     if (g0 != OS_F32 && g0 != OS_BF16 && g0 != OS_FP8E4M3) return OS_ERR_DTYPE;
+    if (m == 0 || l == 0) return OS_OK;   // an empty C: nothing to copy or compute
+    if (!A || !C || (!sym && !B)) return OS_ERR_INVALID_ARG;
     const os_dtype g = sketch_dtype(p, g0);
     const HostPlan h = host_plan(p, m, l, a_t, b_t, opts);
     if (!workspace || ws_bytes < h.a_bytes + h.b_bytes + h.c_bytes + h.mm_bytes + 256) return OS_ERR_WORKSPACE;
-    if (m == 0 || l == 0) return OS_OK;
     int dev = 0;
     OSK_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != p->device) return OS_ERR_INVALID_ARG;

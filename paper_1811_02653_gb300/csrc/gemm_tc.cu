@@ -1022,8 +1022,9 @@ extern "C" os_status oversketch_device_status(void *stream, int32_t *status, int
 extern "C" os_status oversketch_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m,
                                           int64_t n, int64_t K, float alpha, float beta, float *C, int64_t ldc,
                                           void *stream) {
-    if (!A || !B || !C || m < 0 || n < 0 || K < 0 || ldc < n || lda < K || ldb < K) return OS_ERR_INVALID_ARG;
-    if (m == 0 || n == 0) return OS_OK;
+    if (m < 0 || n < 0 || K < 0 || ldc < n || lda < K || ldb < K) return OS_ERR_INVALID_ARG;
+    if (m == 0 || n == 0) return OS_OK;   // an empty C
+    if (!A || !B || !C) return OS_ERR_INVALID_ARG;
     if (K == 0) return OS_ERR_UNSUPPORTED;
     // one K block rounded up to the 64-wide K tile; TMA fills the columns past K with zeros
     BlockList one;
@@ -1038,11 +1039,12 @@ extern "C" os_status oversketch_gemm_masked_blocks(oversketch_plan_t plan, const
                                                    const uint64_t *block_masks, int64_t bm, int64_t bn,
                                                    float beta, float *C, int64_t ldc, void *stream) {
     const Plan *p = reinterpret_cast<const Plan *>(plan);
-    if (!p || !At || !BtT || !C || !block_masks || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
+    if (!p || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
+    if (bm < 256 || bn < 256 || bm % 256 != 0 || bn % 256 != 0) return OS_ERR_UNSUPPORTED;
+    if (m == 0 || l == 0) return OS_OK;   // an empty C: nothing to read or write
+    if (!At || !BtT || !C || !block_masks) return OS_ERR_INVALID_ARG;
     const int64_t z = (int64_t)p->P * p->b;
     if (ldat < z || ldbt < z) return OS_ERR_INVALID_ARG;
-    if (bm < 256 || bn < 256 || bm % 256 != 0 || bn % 256 != 0) return OS_ERR_UNSUPPORTED;
-    if (m == 0 || l == 0) return OS_OK;
     const BlockList all = mask_to_list(~0ull, p->P);
     return launch_pair_bf16(At, ldat, BtT, ldbt, m, l, z, p->b, all, 1.f, beta, C, ldc, as_stream(stream),
                             block_masks, bm, bn, p->P);

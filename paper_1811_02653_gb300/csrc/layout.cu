@@ -81,7 +81,7 @@ using namespace osk;
 extern "C" os_status oversketch_select_transpose(const void *X, os_dtype x_t, int64_t rows, int64_t cols, int64_t ldx,
                                                  uint64_t block_mask, int32_t b, void *Y, os_dtype y_t, int64_t ldy,
                                                  void *stream) {
-    if (!X || !Y || rows < 0 || cols < 0 || ldx < cols) return OS_ERR_INVALID_ARG;
+    if (rows < 0 || cols < 0 || ldx < cols) return OS_ERR_INVALID_ARG;
     if (!float_type(x_t) || !float_type(y_t)) return OS_ERR_DTYPE;
     BlockList kept;
     kept.count = 0;
@@ -96,7 +96,8 @@ extern "C" os_status oversketch_select_transpose(const void *X, os_dtype x_t, in
         ocols = (int64_t)kept.count * b;
     }
     if (ldy < rows) return OS_ERR_INVALID_ARG;
-    if (rows == 0 || ocols == 0) return OS_OK;
+    if (rows == 0 || ocols == 0) return OS_OK;   // an empty Y
+    if (!X || !Y) return OS_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     if (x_t == OS_F32 && y_t == OS_F32) return launch_st<float, float>(X, ldx, rows, ocols, b, kept, Y, ldy, st);
     if (x_t == OS_F32 && y_t == OS_BF16) return launch_st<float, __nv_bfloat16>(X, ldx, rows, ocols, b, kept, Y, ldy, st);
@@ -106,9 +107,10 @@ extern "C" os_status oversketch_select_transpose(const void *X, os_dtype x_t, in
 
 extern "C" os_status oversketch_cast(const void *X, os_dtype x_t, int64_t rows, int64_t cols, int64_t ldx, void *Y,
                                      os_dtype y_t, int64_t ldy, void *stream) {
-    if (!X || !Y || rows < 0 || cols < 0 || ldx < cols || ldy < cols) return OS_ERR_INVALID_ARG;
+    if (rows < 0 || cols < 0 || ldx < cols || ldy < cols) return OS_ERR_INVALID_ARG;
     if (!float_type(x_t) || !float_type(y_t)) return OS_ERR_DTYPE;
-    if (rows == 0 || cols == 0) return OS_OK;
+    if (rows == 0 || cols == 0) return OS_OK;   // an empty Y
+    if (!X || !Y) return OS_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
     if (x_t == OS_F32 && y_t == OS_F32) return launch_cast<float, float>(X, ldx, rows, cols, Y, ldy, st);
     if (x_t == OS_F32 && y_t == OS_BF16) return launch_cast<float, __nv_bfloat16>(X, ldx, rows, cols, Y, ldy, st);

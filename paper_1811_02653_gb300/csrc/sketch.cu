@@ -684,14 +684,13 @@ os_status launch_pack_cols(const T *A, int64_t lda, int64_t m, int64_t n, T *Xs,
 os_status check_out(const Plan *p, int64_t rows, void *Yt, os_dtype out_t, int64_t ldy,
                     float *scales) {
     const int64_t z = (int64_t)p->P * p->b;
-    if (!Yt || rows < 0) return OS_ERR_INVALID_ARG;
+    if (rows < 0) return OS_ERR_INVALID_ARG;
     if (out_t != OS_F32 && out_t != OS_BF16 && out_t != OS_FP8E4M3 && out_t != OS_TF32X2) return OS_ERR_DTYPE;
-    if (ldy < z) return OS_ERR_INVALID_ARG;
-    if (!aligned16(Yt) || (ldy * (int64_t)dtype_size(out_t)) % 16 != 0) return OS_ERR_INVALID_ARG;
-    if (out_t == OS_FP8E4M3) {
-        if (!scales) return OS_ERR_INVALID_ARG;
-        if (p->b % 128 != 0) return OS_ERR_UNSUPPORTED;
-    }
+    if (ldy < z || (ldy * (int64_t)dtype_size(out_t)) % 16 != 0) return OS_ERR_INVALID_ARG;
+    if (out_t == OS_FP8E4M3 && p->b % 128 != 0) return OS_ERR_UNSUPPORTED;
+    if (rows == 0) return OS_OK;   // an empty output: nothing is written
+    if (!Yt || !aligned16(Yt)) return OS_ERR_INVALID_ARG;
+    if (out_t == OS_FP8E4M3 && !scales) return OS_ERR_INVALID_ARG;
     return OS_OK;
 }
 
@@ -735,12 +734,13 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
                            const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
                            cudaStream_t st) {
-    if (!p || !A || m < 0) return OS_ERR_INVALID_ARG;
+    if (!p || m < 0) return OS_ERR_INVALID_ARG;
     if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (a_t != OS_F32 && a_t != OS_BF16) return OS_ERR_DTYPE;
     if (lda < p->n) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_out(p, m, At, out_t, ldat, scales));
     if (m == 0) return OS_OK;
+    if (!A) return OS_ERR_INVALID_ARG;
     if (!ws || ws_bytes < sketch_workspace_bytes(p, m, a_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);
     const float *wts = nullptr;
@@ -758,12 +758,13 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
                             void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
                             void *ws, size_t ws_bytes, cudaStream_t st, const float *row_scale) {
-    if (!p || !B || l < 0) return OS_ERR_INVALID_ARG;
+    if (!p || l < 0) return OS_ERR_INVALID_ARG;
     if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (b_t != OS_F32 && b_t != OS_BF16) return OS_ERR_DTYPE;
     if (ldb < l) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_out(p, l, BtT, out_t, ldbt, scales));
     if (l == 0) return OS_OK;
+    if (!B) return OS_ERR_INVALID_ARG;
     // FP32 input with 16-byte aligned rows: gather whole 128-wide strips in place,
     // and pack only a ragged remainder of fewer than 128 columns.
     const bool direct = b_t == OS_F32 && aligned16(B) && ldb % 4 == 0 && ldb * 4 < (int64_t(1) << 32) &&
@@ -800,12 +801,13 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
 
 os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t ldt, uint64_t mask,
                              float scale, void *dX, os_dtype x_t, int64_t ldx, cudaStream_t st) {
-    if (!p || !T || !dX || m < 0) return OS_ERR_INVALID_ARG;
+    if (!p || m < 0) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_mask(mask, p->P));
     const int kcnt = __builtin_popcountll(mask);
     if (ldt < (int64_t)kcnt * p->b || ldx < p->n) return OS_ERR_INVALID_ARG;
     if (x_t != OS_F32 && x_t != OS_BF16) return OS_ERR_DTYPE;
-    if (m == 0) return OS_OK;
+    if (m == 0) return OS_OK;   // an empty dX
+    if (!T || !dX) return OS_ERR_INVALID_ARG;
     const BlockList kept = mask_to_list(mask, p->P);
     // rows of T staged per CTA: the most that keep two or more CTAs per SM (up to
     // 96 KB each), else one row in up to 200 KB, else the unstaged kernel
@@ -846,11 +848,12 @@ os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t l
 
 os_status unsketch_rows_impl(const Plan *p, const float *U, int64_t l, int64_t ldu, uint64_t mask,
                              float scale, void *dG, os_dtype g_t, int64_t ldg, cudaStream_t st) {
-    if (!p || !U || !dG || l < 0) return OS_ERR_INVALID_ARG;
+    if (!p || l < 0) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_mask(mask, p->P));
     if (ldu < l || ldg < l) return OS_ERR_INVALID_ARG;
     if (g_t != OS_F32 && g_t != OS_BF16) return OS_ERR_DTYPE;
-    if (l == 0) return OS_OK;
+    if (l == 0) return OS_OK;   // an empty dG
+    if (!U || !dG) return OS_ERR_INVALID_ARG;
     const BlockList kept = mask_to_list(mask, p->P);
     dim3 grid((unsigned)((p->n + 7) / 8), (unsigned)((l + 1023) / 1024));
     if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;

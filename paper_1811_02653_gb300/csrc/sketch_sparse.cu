@@ -462,19 +462,17 @@ bool sketch_left_sparse_fits(const Plan *p, uint64_t block_mask) {
 os_status sketch_left_sparse_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda, void *At,
                                   os_dtype out_t, int64_t ldat, float *scales, const float *col_scale,
                                   uint64_t block_mask, cudaStream_t st) {
-    if (!p || !A || !At || m < 0) return OS_ERR_INVALID_ARG;
+    if (!p || m < 0) return OS_ERR_INVALID_ARG;
     if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (a_t != OS_F32 && a_t != OS_BF16) return OS_ERR_DTYPE;
     if (out_t != OS_F32 && out_t != OS_BF16 && out_t != OS_FP8E4M3 && out_t != OS_TF32X2) return OS_ERR_DTYPE;
     const int64_t z = (int64_t)p->P * p->b;
-    if (lda < p->n || ldat < z) return OS_ERR_INVALID_ARG;
-    if (!aligned16(At) || (ldat * (int64_t)dtype_size(out_t)) % 16 != 0) return OS_ERR_INVALID_ARG;
-    if (out_t == OS_FP8E4M3) {
-        if (!scales) return OS_ERR_INVALID_ARG;
-        if (p->b % 128 != 0) return OS_ERR_UNSUPPORTED;
-    }
+    if (lda < p->n || ldat < z || (ldat * (int64_t)dtype_size(out_t)) % 16 != 0) return OS_ERR_INVALID_ARG;
+    if (out_t == OS_FP8E4M3 && p->b % 128 != 0) return OS_ERR_UNSUPPORTED;
     if (!sketch_left_sparse_fits(p, block_mask)) return OS_ERR_UNSUPPORTED;
-    if (m == 0) return OS_OK;
+    if (m == 0) return OS_OK;   // an empty output
+    if (!A || !At || !aligned16(At)) return OS_ERR_INVALID_ARG;
+    if (out_t == OS_FP8E4M3 && !scales) return OS_ERR_INVALID_ARG;
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
     if (a_t == OS_F32)
         return launch_sparse<float>((const float *)A, lda, m, p, blocks, col_scale, At, out_t, ldat, scales, st);

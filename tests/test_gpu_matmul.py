@@ -113,3 +113,31 @@ def test_square_workload_sampled_fp32(ops):
     C_ref = oracle.oversketch(Ar, Bc, h, s, w.b, w.mask)
     C_s = C[rows][:, cols].cpu().numpy()
     assert oracle.rel_frob(C_s, C_ref) <= 1e-5
+
+
+def test_empty_operands(ops):
+    # an empty C (m = 0 or l = 0) is OS_OK with nothing launched, even where the
+    # empty tensors carry no storage
+    n, b, N, e = 512, 64, 4, 1
+    p = ops.plan(n, b, N, e, 0)
+    mask = 0b11011
+    A0 = torch.empty((0, n), device="cuda")
+    B = torch.randn((n, 96), device="cuda")
+    A = torch.randn((64, n), device="cuda")
+    B0 = torch.empty((n, 0), device="cuda")
+    for gd in ("f32", "bf16"):
+        assert ops.matmul(p, A0, B, mask, gd).shape == (0, 96)
+        assert ops.matmul(p, A, B0, mask, gd).shape == (64, 0)
+    assert ops.matmul(p, A0, None, mask, "bf16", symmetric=True).shape == (0, 0)
+    At, _ = ops.sketch_left(p, A0, "bf16")
+    BtT, _ = ops.sketch_right(p, B0, "bf16")
+    assert At.shape == (0, p.z) and BtT.shape == (0, p.z)
+    Bt1, _ = ops.sketch_right(p, B, "bf16")
+    assert ops.gemm_masked(p, At, Bt1, mask).shape == (0, 96)
+    masks = torch.full((1, 1), mask, dtype=torch.int64, device="cuda")
+    assert ops.gemm_masked_blocks(p, At, Bt1, masks, 256, 256).shape == (0, 96)
+    T0 = torch.empty((0, 4 * b), device="cuda")
+    assert ops.unsketch_cols(p, T0, mask, 1.0).shape == (0, n)
+    C = ops.matmul_host(p, torch.empty((0, n)), torch.randn((n, 96)), mask, "bf16")
+    torch.cuda.synchronize()
+    assert C.shape == (0, 96)
