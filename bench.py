@@ -8,8 +8,15 @@ dtype), masked block-sum GEMM with scale 1/k.  Inputs (8.6 GB) exceed L2, so
 no flush is needed between steps.  The plan (hash + bucket-CSR) is built once
 before timing, as the same S is reused across products.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|f32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|f32|fp8]
   python bench.py --impl reference ...   # the FP64 CPU oracle on a sample
+  python bench.py --workload hessian|batched|autograd|lp|sec51   # the other workloads
+
+The other workloads: the interior-point normal matrix A D A^T with a 1 %-dense
+A (hessian); 256 uneven products in one CUDA graph (batched); a BF16 forward
+and backward (autograd); the LP of Sec. 5.2 with its sketched Hessian and
+100-iteration barrier runs (lp); the accuracy study of Sec. 5.1 on
+A(x, y) = x + y (sec51).
 
 Multi-GPU (torchrun): every rank runs its own independent product (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
