@@ -362,7 +362,17 @@ def run_ours(args):
     es = {"bf16": 2, "f32": 4, "fp8": 1, "tf32x2": 8}[sd]
     n_kept = w.k
     right_bytes = w.n * w.l * 4 + w.l * n_kept * w.b * es
+    left_bytes = w.m * w.n * 4 + w.m * n_kept * w.b * es
     gemm_flop = 2.0 * w.m * n_kept * w.b * w.l
+    # the sketches against HBM (algorithmic bytes: operand read once, kept blocks written
+    # once) and as signed adds (rows * n * k); their own bound is the L2 gather (DESIGN)
+    hbm = peaks.get("hbm_gbs")
+    sketch_roofs = {}
+    for side, nbytes, rows, t_ms in (("left", left_bytes, w.m, t_left), ("right", right_bytes, w.l, t_right)):
+        gbs = nbytes / (t_ms * 1e-3) / 1e9
+        sketch_roofs[side] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                              "frac": gbs / hbm if hbm else None, "algorithmic_bytes": nbytes,
+                              "signed_adds_per_s": float(rows) * w.n * n_kept / (t_ms * 1e-3)}
     phases = {"sketch_left (pack + gather)": t_left, "sketch_right (pack + gather)": t_right,
               "gemm_masked": t_gemm}
     if t_gemm >= t_right:
@@ -443,7 +453,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": gd, "data": "synthetic (seeded; no dataset)",
             "config": _config(w, args),
             "phases_ms": {k_: round(v_, 4) for k_, v_ in phases.items()},
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "sketch_rooflines": sketch_roofs, "cpu_baseline": cpu,
             "e2e": {"value": _job_value(flop_eff, e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": 4 * args.steps, "clocks": clk, "error": err, "exact_gemm": exact}
