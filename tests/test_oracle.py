@@ -448,3 +448,18 @@ def test_per_block_kept_sets_keep_the_expected_error():
     errs = np.array(errs)
     expect = oracle.expected_sq_error(A, B, N, b)
     assert abs(errs.mean() - expect) < 5 * errs.std() / np.sqrt(len(errs))
+
+
+def test_sec51_operands_and_exact_product():
+    # Sec. 5.1's A(x, y) = x + y: the factors reproduce A, B = A^T, and the closed-form
+    # A A^T used as the exact reference equals a plain FP64 product
+    torch = pytest.importorskip("torch")
+    from paper_1811_02653_gb300 import workloads
+    m, n = 40, 300
+    A, B, AB = workloads.sec51_device(m, n, "cpu")
+    U, V = workloads.sec51_factors(m, n)
+    A64 = U @ V.T
+    assert np.array_equal(A.numpy().astype(np.float64), A64)
+    assert np.array_equal(B.numpy(), A.numpy().T)
+    ref = A64 @ A64.T
+    assert np.allclose(AB.numpy().astype(np.float64), ref, rtol=2.0 ** -23, atol=0)
