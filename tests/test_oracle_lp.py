@@ -79,3 +79,36 @@ def test_straggler_masks():
     s = workloads.straggler_block_masks(20, 2, 5, 5, 3, 0, shared=True)
     assert len(set(s.ravel().tolist())) == 1 and bin(int(s[0, 0])).count("1") == 18
     assert (workloads.straggler_block_masks(20, 1, 5, 5, 3, 0) == m).all()
+
+
+def test_barrier_follows_the_central_path_of_a_box():
+    # min x s.t. 0 <= x <= 1: the barrier tau x - log x - log(1 - x) is minimised at the
+    # root of tau x^2 - (tau + 2) x + 1 = 0 in (0, 1); ten Newton steps per tau land on it
+    A = np.array([[-1.0], [1.0]])
+    b = np.array([0.0, 1.0])
+    c = np.array([1.0])
+    for stages in (1, 3, 6):
+        x, _ = lp.barrier_lp(A, b, c, np.array([0.5]), iters=10 * stages, tau0=1.0, every=10)
+        tau = 2.0 ** (stages - 1)
+        centre = ((tau + 2) - np.sqrt((tau + 2) ** 2 - 4 * tau)) / (2 * tau)
+        assert abs(x[0] - centre) < 1e-9
+
+
+def test_gpu_solver_newton_system_matches_the_oracle_rule():
+    # the GPU solver's Newton system (FP32 Cholesky with the shift search) chooses the
+    # same shift as the oracle's FP64 rule and gives the same direction, on the host
+    torch = pytest.importorskip("torch")
+    from paper_1811_02653_gb300 import lp as glp
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.standard_normal((6, 6)))
+    for lam_min in (0.3, -0.5):                     # positive definite, then indefinite
+        H = Q @ np.diag([lam_min, 1.0, 2.0, 3.0, 5.0, 8.0]) @ Q.T
+        H = H + 0.01 * rng.standard_normal((6, 6))   # the sketched Hessian is not symmetric
+        g = rng.standard_normal(6)
+        solver = object.__new__(glp.SketchedBarrierLP)
+        solver.m, solver.device, solver._I = 6, torch.device("cpu"), None
+        hist = glp.LPHistory()
+        d_gpu = solver.newton_direction(torch.tensor(H, dtype=torch.float32), torch.tensor(g), hist).numpy()
+        d_ref = lp.newton_direction(H, g)
+        assert np.allclose(d_gpu, d_ref, rtol=1e-4, atol=1e-5)
+        assert hist.shifts == (1 if lam_min < 0 else 0)
