@@ -9,8 +9,9 @@ part of the Hessian, Jacobi-equilibrated; when that is not positive definite (a
 sketched Hessian whose blocks keep different sketch blocks need not be) the
 smallest shift in 0, 1e-8, 1e-7, ... times the identity that makes it so is
 added -- the paper does not say how an indefinite system is treated, this is
-the reading both solvers share.  The step size eta comes from a backtracking
-line search that keeps every slack positive (Armijo condition with parameter
+the reading both solvers share; a non-finite system, or one that no shift up
+to 1e8 repairs, raises NewtonSystemError instead of looping.  The step size eta
+comes from a backtracking line search that keeps every slack positive (Armijo condition with parameter
 1/4, halving).  Plain FP64 numpy; shares no code with the GPU solver.  The
 pinned fact: after the last centring step at barrier weight tau the objective
 is within n / tau of the LP optimum (the barrier's duality gap).
@@ -27,19 +28,38 @@ def barrier_objective(A, b, c, x, tau):
     return tau * float(c @ x) - float(np.sum(np.log(s)))
 
 
+class NewtonSystemError(ValueError):
+    """The Newton system cannot be solved: a non-finite Hessian or gradient, or no
+    shift up to MAX_SHIFT makes the equilibrated system positive definite."""
+
+
+MAX_SHIFT = 1e8
+SHIFTS = (0.0,) + tuple(10.0 ** p for p in range(-8, 9))      # 0, 1e-8, ..., 1e8
+
+
 def newton_direction(H, g):
     """-(H_sym + shift D)^{-1} g with D = diag(H_sym) and the smallest shift of
-    0, 1e-8, 1e-7, ... for which the equilibrated system is positive definite."""
+    0, 1e-8, 1e-7, ..., 1e8 for which the equilibrated system is positive
+    definite.  A row whose diagonal entry is not positive is left unscaled (a
+    Hessian of Sec. 5.2, sketched or not, has a non-negative diagonal: each
+    diagonal entry is a sum of squares).  Raises NewtonSystemError for a
+    non-finite H or g, or when no shift up to 1e8 factorises."""
+    H = np.asarray(H, np.float64)
+    g = np.asarray(g, np.float64)
+    if not (np.all(np.isfinite(H)) and np.all(np.isfinite(g))):
+        raise NewtonSystemError("non-finite Hessian or gradient")
     Hs = 0.5 * (H + H.T)
-    d = 1.0 / np.sqrt(np.maximum(np.diag(Hs), np.finfo(np.float64).tiny))
+    dH = np.diag(Hs)
+    d = np.where(dH > 0.0, 1.0 / np.sqrt(np.where(dH > 0.0, dH, 1.0)), 1.0)
     He = Hs * d[:, None] * d[None, :]
-    shift = 0.0
-    while True:
+    for shift in SHIFTS:
         try:
             L = np.linalg.cholesky(He + shift * np.eye(len(d)))
             break
         except np.linalg.LinAlgError:
-            shift = 1e-8 if shift == 0.0 else shift * 10.0
+            continue
+    else:
+        raise NewtonSystemError("no shift up to 1e8 makes the Newton system positive definite")
     y = np.linalg.solve(L.T, np.linalg.solve(L, g * d))
     return -(y * d)
 

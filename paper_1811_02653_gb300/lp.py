@@ -20,8 +20,9 @@ solve are PyTorch (cuBLAS / cuSOLVER) around that.  A sketched Hessian whose
 blocks keep different sketch blocks is neither symmetric nor, in general,
 positive semidefinite (it is no longer a Gram matrix).  The Newton system uses
 its symmetric part, Jacobi-equilibrated and factorised by Cholesky in FP32
-with the smallest shift of 0, 1e-8, 1e-7, ... times the identity for which the
-factorisation succeeds.
+with the smallest shift of 0, 1e-8, 1e-7, ..., 1e8 times the identity for which
+the factorisation succeeds (a non-finite system, or one that no such shift
+repairs, raises NewtonSystemError).
 """
 from __future__ import annotations
 
@@ -32,6 +33,15 @@ import numpy as np
 import torch
 
 from . import ops
+
+
+MAX_SHIFT = 1e8
+SHIFTS = (0.0,) + tuple(10.0 ** p for p in range(-8, 9))      # 0, 1e-8, ..., 1e8
+
+
+class NewtonSystemError(ValueError):
+    """The Newton system cannot be solved: a non-finite Hessian or gradient, or no
+    shift up to MAX_SHIFT makes the equilibrated system positive definite."""
 
 
 @dataclass
@@ -90,19 +100,25 @@ class SketchedBarrierLP:
     # -- the Newton system ----------------------------------------------------
     def newton_direction(self, H: torch.Tensor, g: torch.Tensor, hist: LPHistory) -> torch.Tensor:
         """-(H_sym + shift D)^{-1} g, D = diag(H_sym), with the smallest shift of
-        0, 1e-8, 1e-7, ... for which the equilibrated system factorises."""
+        0, 1e-8, 1e-7, ..., 1e8 for which the equilibrated system factorises
+        (rows with a non-positive diagonal entry are left unscaled).  Raises
+        NewtonSystemError for a non-finite H or g, or when no shift up to 1e8
+        factorises, instead of searching forever."""
+        if not (bool(torch.isfinite(H).all()) and bool(torch.isfinite(g).all())):
+            raise NewtonSystemError("non-finite Hessian or gradient")
         Hs = 0.5 * (H + H.t())
-        dg = Hs.diagonal().clamp_min(torch.finfo(torch.float32).tiny).rsqrt()
+        dH = Hs.diagonal()
+        pos = dH > 0
+        dg = torch.where(pos, torch.where(pos, dH, torch.ones_like(dH)).rsqrt(), torch.ones_like(dH))
         Heq = Hs * dg[:, None] * dg[None, :]
         rhs = (g.float() * dg)[:, None]
-        shift = 0.0
-        while True:
+        for shift in SHIFTS:
             L, info = torch.linalg.cholesky_ex(Heq if shift == 0.0 else Heq + shift * self._eye())
             if int(info) == 0:
                 hist.shifts += shift > 0.0
                 y = torch.cholesky_solve(rhs, L)[:, 0]
                 return -(y.double() * dg.double())
-            shift = 1e-8 if shift == 0.0 else shift * 10.0
+        raise NewtonSystemError("no shift up to 1e8 makes the Newton system positive definite")
 
     def _eye(self):
         if getattr(self, "_I", None) is None:

@@ -112,3 +112,39 @@ def test_gpu_solver_newton_system_matches_the_oracle_rule():
         d_ref = lp.newton_direction(H, g)
         assert np.allclose(d_gpu, d_ref, rtol=1e-4, atol=1e-5)
         assert hist.shifts == (1 if lam_min < 0 else 0)
+
+
+@pytest.mark.parametrize("case", ["nan", "inf", "negative_diagonal", "hopeless"])
+def test_newton_system_errors_instead_of_looping(case):
+    # both solvers refuse a Newton system they cannot solve, instead of widening the
+    # shift forever: a NaN or Inf Hessian, and one no shift up to 1e8 repairs
+    # (a diagonal entry of -1e12 stays negative after equilibration-free scaling);
+    # a negative diagonal entry alone is left unscaled and repaired by a shift
+    torch = pytest.importorskip("torch")
+    from paper_1811_02653_gb300 import lp as glp
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((5, 5))
+    H = M @ M.T + 5 * np.eye(5)
+    g = rng.standard_normal(5)
+    if case == "nan":
+        H[1, 2] = np.nan
+    elif case == "inf":
+        H[0, 0] = np.inf
+    elif case == "negative_diagonal":
+        H[3, 3] = -0.5
+    else:
+        H[2, 2] = -1e12
+    solver = object.__new__(glp.SketchedBarrierLP)
+    solver.m, solver.device, solver._I = 5, torch.device("cpu"), None
+    if case == "negative_diagonal":
+        d_ref = lp.newton_direction(H, g)
+        assert np.all(np.isfinite(d_ref))
+        hist = glp.LPHistory()
+        d_gpu = solver.newton_direction(torch.tensor(H, dtype=torch.float32), torch.tensor(g), hist).numpy()
+        assert np.all(np.isfinite(d_gpu)) and hist.shifts == 1
+        assert np.allclose(d_gpu, d_ref, rtol=1e-3, atol=1e-5)
+        return
+    with pytest.raises(lp.NewtonSystemError):
+        lp.newton_direction(H, g)
+    with pytest.raises(glp.NewtonSystemError):
+        solver.newton_direction(torch.tensor(H, dtype=torch.float32), torch.tensor(g), glp.LPHistory())
