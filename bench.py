@@ -10,9 +10,10 @@ before timing, as the same S is reused across products.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|f32|fp8]
   python bench.py --impl reference ...   # the FP64 CPU oracle on a sample
-  python bench.py --workload hessian|batched|autograd|lp|sec51   # the other workloads
+  python bench.py --workload small|hessian|batched|autograd|lp|sec51   # the other workloads
 
-The other workloads: the interior-point normal matrix A D A^T with a 1 %-dense
+The other workloads: the minimum slice 512x4096x512 timed with L2 flushed and
+warm (small); the interior-point normal matrix A D A^T with a 1 %-dense
 A (hessian); 256 uneven products in one CUDA graph (batched); a BF16 forward
 and backward (autograd); the LP of Sec. 5.2 with its sketched Hessian and
 100-iteration barrier runs (lp); the accuracy study of Sec. 5.1 on
@@ -213,6 +214,24 @@ def run_reference(args):
     return 0
 
 
+def _sketch_dtype(gemm_dtype: str, b: int) -> str:
+    """Sketch output dtype of a GEMM dtype: the FP32 product runs as 3xTF32 on the
+    tensor cores, so its sketches emit hi/lo planes."""
+    return "tf32x2" if gemm_dtype == "f32" and b % 32 == 0 else gemm_dtype
+
+
+def _oracle_product_as(oracle, f, At_r, Bt_c, b, mask):
+    """The oracle's masked product with the operand rounding of GEMM dtype f
+    (BF16: RNE of the sketch; FP8: per-(row, 128-column) UE8M0 scale + E4M3)."""
+    if f == "bf16":
+        return oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(Bt_c), b, mask)
+    if f == "fp8":
+        Aq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(At_r))
+        Bq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(Bt_c.T)).T
+        return oracle.masked_product(Aq, Bq, b, mask)
+    return oracle.masked_product(At_r, Bt_c, b, mask)
+
+
 def _workload(args):
     from paper_1811_02653_gb300 import workloads as W
     if args.shape:
@@ -255,10 +274,16 @@ def run_ours(args):
     B = Bt_h.to(dev).t().contiguous()                              # n x l row-major
     B_h = B.cpu().pin_memory()
     del Bt_h
+    # plan creation (hash tables + bucket-CSR; oversketch_plan synchronises), timed
+    # on its own: the same S serves every product, so it is outside the step
+    plan_s = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        ops.plan(w.n, w.b, w.N, w.e, w.hash_seed).destroy()
+        plan_s.append(time.perf_counter() - t0)
     p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
     gd = args.dtype
-    # the FP32 product runs as 3xTF32 on the tensor cores: sketches emit hi/lo planes
-    sd = "tf32x2" if gd == "f32" and w.b % 32 == 0 else gd
+    sd = _sketch_dtype(gd, w.b)
     z = p.z
     At, a_sc = ops.sketch_left(p, A, sd)
     BtT, b_sc = ops.sketch_right(p, B, sd)
@@ -332,6 +357,26 @@ def run_ours(args):
     h2d = A_h.numel() * 4 + B_h.numel() * 4
     d2h = C_h.numel() * 4
 
+    # ---- the other GEMM dtypes on the same inputs (same three calls, own sketch buffers) ----
+    forms = {}
+    if not args.no_forms:
+        for f in [x for x in ("f32", "fp8", "bf16") if x != gd]:
+            sf = _sketch_dtype(f, w.b)
+            Af, asf = ops.sketch_left(p, A, sf, workspace=ws_pack)
+            Bf, bsf = ops.sketch_right(p, B, sf, workspace=ws_pack)
+            phases_f = [("sketch_left", lambda: ops.sketch_left(p, A, sf, out=Af, scales=asf, workspace=ws_pack,
+                                                                 block_mask=w.mask)),
+                        ("sketch_right", lambda: ops.sketch_right(p, B, sf, out=Bf, scales=bsf, block_mask=w.mask,
+                                                                   workspace=ws_pack)),
+                        ("gemm_masked", lambda: ops.gemm_masked(p, Af, Bf, w.mask, C=C, a_scales=asf, b_scales=bsf,
+                                                                dtype=sf))]
+            ms_f, per_f, _ = _time_phases(phases_f, max(3, min(args.steps, 10)), 2, world, sample_clocks=False)
+            forms[f] = {"ms_per_step": ms_f, "tflops": _job_value(2.0 * w.m * w.n * w.l, ms_f, world),
+                        "phases_ms": {k_: round(v_, 4) for k_, v_ in per_f.items()},
+                        "sketch_dtype": sf}
+            del Af, Bf, asf, bsf
+        torch.cuda.synchronize()
+
     # ---- exact GEMM on the same GPU: the same tcgen05 kernel over K = n (all blocks kept) ----
     exact = None
     if not args.no_exact and w.n % 64 == 0 and w.n // 64 <= 4096:
@@ -342,13 +387,14 @@ def run_ours(args):
             pe = ops.plan(w.n, bx, w.n // bx, 0, 0)
             full = (1 << (w.n // bx)) - 1
             Cx = torch.empty((w.m, w.l), dtype=torch.float32, device=dev)
-            ops.gemm_masked(pe, A16, Bt16, full, alpha=1.0, C=Cx)
+            # every block kept: alpha = k cancels the library's 1/k, giving A.B itself
+            ops.gemm_masked(pe, A16, Bt16, full, alpha=float(w.n // bx), C=Cx)
             torch.cuda.synchronize()
             x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             reps = 3
             x0.record(stream)
             for _ in range(reps):
-                ops.gemm_masked(pe, A16, Bt16, full, alpha=1.0, C=Cx)
+                ops.gemm_masked(pe, A16, Bt16, full, alpha=float(w.n // bx), C=Cx)
             x1.record(stream)
             torch.cuda.synchronize()
             ex_ms = x0.elapsed_time(x1) / reps
@@ -425,24 +471,25 @@ def run_ours(args):
             Bc = np.ascontiguousarray(w.right_cols(cols).T, dtype=np.float64)
             At_r = oracle.sketch_left(Ar, h, s, w.b)
             Bt_c = oracle.sketch_right(Bc, h, s, w.b)
-            if gd == "bf16":
-                C_or = oracle.masked_product(oracle.round_bf16(At_r), oracle.round_bf16(Bt_c), w.b, w.mask)
-            elif gd == "fp8":
-                Aq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(At_r))
-                Bq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(Bt_c.T)).T
-                C_or = oracle.masked_product(Aq, Bq, w.b, w.mask)
-            else:
-                C_or = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
             C_or_exact_sketch = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
-            ops.matmul(p, A, B, w.mask, gd, C=C, workspace=ws_mm)
-            C_s = C[rows][:, cols].cpu().numpy().astype(np.float64)
             AB = Ar @ Bc
+
+            def sampled_error(f):
+                C_or = _oracle_product_as(oracle, f, At_r, Bt_c, w.b, w.mask)
+                ws_f = torch.empty(ops.workspace_size(p, w.m, w.l, torch.float32, f), dtype=torch.uint8, device=dev)
+                ops.matmul(p, A, B, w.mask, f, C=C, workspace=ws_f)
+                C_s = C[rows][:, cols].cpu().numpy().astype(np.float64)
+                del ws_f
+                return oracle.rel_frob(C_s, C_or), oracle.rel_frob(C_s, AB)
+
             if exact is not None:
                 exact["vs_exact_rel_frob"] = oracle.rel_frob(exact_C[rows][:, cols].cpu().numpy(), Ar @ Bc)
-            err = {"vs_oracle_rel_frob": oracle.rel_frob(C_s, C_or),
-                   "vs_exact_rel_frob": oracle.rel_frob(C_s, AB),
+            e_or, e_ex = sampled_error(gd)
+            err = {"vs_oracle_rel_frob": e_or, "vs_exact_rel_frob": e_ex,
                    "oracle_sketch_vs_exact_rel_frob": oracle.rel_frob(C_or_exact_sketch, AB),
                    "sample": f"{len(rows)}x{len(cols)} entries of C; oracle emulates {gd} operand rounding"}
+            for f, d in forms.items():
+                d["vs_oracle_rel_frob"], d["vs_exact_rel_frob"] = sampled_error(f)
         rs = args.ref_sample or calibrated_sample(w, 10.0)
         t_cpu, threads, desc = oracle_sample_time(w, rs, rs)
         cpu = {"value": 2.0 * rs * w.n * rs / t_cpu / 1e12, "unit": UNIT,
@@ -456,7 +503,10 @@ def run_ours(args):
             "roofline": roof, "sketch_rooflines": sketch_roofs, "cpu_baseline": cpu,
             "e2e": {"value": _job_value(flop_eff, e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 4 * args.steps, "clocks": clk, "error": err, "exact_gemm": exact}
+            "gpu_launches": 4 * args.steps, "clocks": clk, "error": err, "exact_gemm": exact,
+            "forms": forms,
+            "plan_ms": {"median": statistics.median(plan_s) * 1e3, "runs": len(plan_s),
+                        "what": "oversketch_plan host wall time: table allocation, hash, bucket-CSR, synchronise"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -468,7 +518,7 @@ def run_ours(args):
 # the other workloads (--workload): parity cases of the suite, measured the same way
 # ----------------------------------------------------------------------------
 
-def _time_phases(phases, steps, warmup, world):
+def _time_phases(phases, steps, warmup, world, sample_clocks=True):
     """W untimed warm-up steps, then K timed steps bracketed by a barrier and a
     synchronize, with one CUDA event per phase boundary on the launching stream.
     Returns (ms per step (max over ranks), {phase: mean ms}, clocks)."""
@@ -479,9 +529,10 @@ def _time_phases(phases, steps, warmup, world):
             fn()
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)] for _ in range(steps)]
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    time.sleep(0.3)
+    clocks = ClockSampler(torch.cuda.current_device()) if sample_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
     _barrier(world)
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -494,7 +545,7 @@ def _time_phases(phases, steps, warmup, world):
     t1.record(stream)
     torch.cuda.synchronize()
     _barrier(world)
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     total = _max_over_ranks(t0.elapsed_time(t1), world)
     per = {name: statistics.mean(e[q].elapsed_time(e[q + 1]) for e in ev) for q, (name, _) in enumerate(phases)}
     return total / steps, per, clk
@@ -537,6 +588,134 @@ def _hbm_roof(peaks, peak_kind, bytes_, ms, kernel):
     return {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk, "traffic": None,
             "kernel": kernel, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)",
             "algorithmic_per_launch": {"bytes": bytes_}}
+
+
+def run_small(args):
+    """The minimum slice (512 x 4096 x 512 FP32, b=256, N=4, e=1, block 2 dropped):
+    16 MB of inputs fit in L2, so the step is timed twice -- back to back with
+    the inputs warm in L2, and with a 512 MB buffer written between steps (the
+    L2 flushed; only the step is inside the events).  `value` is the flushed rate."""
+    import torch
+    from paper_1811_02653_gb300 import build, ops
+    from paper_1811_02653_gb300 import workloads as W
+    world, rank, _ = _init_dist()
+    build.build()
+    w = W.SMALL
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A_h = torch.from_numpy(w.left()).pin_memory()
+    B_h = torch.from_numpy(w.right()).pin_memory()
+    A, B = A_h.to(dev), B_h.to(dev)
+    plan_s = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        ops.plan(w.n, w.b, w.N, w.e, w.hash_seed).destroy()
+        plan_s.append(time.perf_counter() - t0)
+    p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
+    gd = args.dtype
+    sd = _sketch_dtype(gd, w.b)
+    At, a_sc = ops.sketch_left(p, A, sd)
+    BtT, b_sc = ops.sketch_right(p, B, sd)
+    C = torch.empty((w.m, w.l), dtype=torch.float32, device=dev)
+    ws = torch.empty(max(ops.sketch_workspace(p, w.m), ops.sketch_workspace(p, w.l)), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    phases = [("sketch_left", lambda: ops.sketch_left(p, A, sd, out=At, scales=a_sc, workspace=ws, block_mask=w.mask)),
+              ("sketch_right", lambda: ops.sketch_right(p, B, sd, out=BtT, scales=b_sc, block_mask=w.mask,
+                                                         workspace=ws)),
+              ("gemm_masked", lambda: ops.gemm_masked(p, At, BtT, w.mask, C=C, a_scales=a_sc, b_scales=b_sc,
+                                                      dtype=sd))]
+    flop = 2.0 * w.m * w.n * w.l
+    # warm L2: steps back to back
+    warm_ms, warm_per, _ = _time_phases(phases, max(args.steps, 50), args.warmup, world, sample_clocks=False)
+    # flushed L2: a 512 MB write between steps, outside the per-step events
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        for _, fn in phases:
+            fn()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    _barrier(world)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        for q, (_, fn) in enumerate(phases):
+            ev[k][q].record(stream)
+            fn()
+        ev[k][3].record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    clk = clocks.stop()
+    fl_ms = _max_over_ranks(statistics.median(e[0].elapsed_time(e[3]) for e in ev), world)
+    fl_per = {name: statistics.median(e[q].elapsed_time(e[q + 1]) for e in ev) for q, (name, _) in enumerate(phases)}
+    # the dominant phase of the flushed step against its roofline (algorithmic work)
+    peaks, peak_kind = _peaks()
+    es = {"bf16": 2, "f32": 4, "fp8": 1, "tf32x2": 8}[sd]
+    dom = max(fl_per, key=fl_per.get)
+    if dom == "gemm_masked":
+        gflop = 2.0 * w.m * w.k * w.b * w.l
+        ach = gflop / (fl_per[dom] * 1e-3) / 1e12
+        pk = peaks.get("bf16_tflops") * {"bf16": 1.0, "fp8": 2.0, "tf32x2": 1.0 / 6.0}.get(sd, 1.0)
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": None, "kernel": f"masked GEMM ({sd})",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)", "algorithmic_per_launch": {"flop": gflop}}
+    else:
+        rows = w.m if dom == "sketch_left" else w.l
+        roof = _hbm_roof(peaks, peak_kind, rows * w.n * 4 + rows * w.k * w.b * es, fl_per[dom],
+                         f"{dom} (pack + gather)")
+    # end to end through the C ABI with pinned host buffers
+    C_h = torch.empty((w.m, w.l), dtype=torch.float32).pin_memory()
+    ws_host = torch.empty(ops.matmul_host_workspace(p, w.m, w.l, gemm_dtype=gd), dtype=torch.uint8, device=dev)
+    ops.matmul_host(p, A_h, B_h, w.mask, gd, C=C_h, workspace=ws_host)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(10, args.steps)
+    s0.record(stream)
+    for _ in range(reps):
+        ops.matmul_host(p, A_h, B_h, w.mask, gd, C=C_h, workspace=ws_host)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = _max_over_ranks(s0.elapsed_time(s1) / reps, world)
+    err = cpu = None
+    if _cpu_leg(args, rank, world):
+        import oracle
+        h, s_ = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
+        A64, B64 = w.left().astype(np.float64), w.right().astype(np.float64)
+        t0 = time.perf_counter()
+        reps_cpu = 0
+        while time.perf_counter() - t0 < 10.0 or reps_cpu < 1:
+            At_r = oracle.sketch_left(A64, h, s_, w.b)
+            Bt_c = oracle.sketch_right(B64, h, s_, w.b)
+            C_or64 = oracle.masked_product(At_r, Bt_c, w.b, w.mask)
+            reps_cpu += 1
+        t_cpu = (time.perf_counter() - t0) / reps_cpu
+        cpu = {"value": flop / t_cpu / 1e12, "unit": UNIT,
+               "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+               "sample": f"the whole workload (512x4096x512: both sketches and the masked product in FP64), "
+                         f"{reps_cpu} runs"}
+        if not args.no_check:
+            ops.matmul(p, A, B, w.mask, gd, C=C)
+            Cg = C.cpu().numpy().astype(np.float64)
+            err = {"vs_oracle_rel_frob": oracle.rel_frob(Cg, _oracle_product_as(oracle, gd, At_r, Bt_c, w.b, w.mask)),
+                   "vs_exact_rel_frob": oracle.rel_frob(Cg, A64 @ B64),
+                   "oracle_sketch_vs_exact_rel_frob": oracle.rel_frob(C_or64, A64 @ B64),
+                   "sample": f"all of C; oracle emulates {gd} operand rounding"}
+    cfg = {"workload": w.name, "m": w.m, "n": w.n, "l": w.l, "b": w.b, "N": w.N, "e": w.e,
+           "kept_blocks": [j for j in range(w.P) if (w.mask >> j) & 1], "gemm_dtype": gd, "input_dtype": "f32",
+           "l2": "inputs (16.8 MB) fit in L2: value is timed with a 512 MB buffer written between steps "
+                 "(L2 flushed); warm_l2 gives the back-to-back rate",
+           "parallelism": f"replicas{world}"}
+    line = _line(args, w.name, _job_value(flop, fl_ms, world), fl_ms, gd, cfg, fl_per, roof, cpu,
+                 {"value": _job_value(flop, e2e_ms, world), "unit": UNIT, "ms_per_step": e2e_ms,
+                  "h2d_bytes_per_step": A_h.numel() * 4 + B_h.numel() * 4, "d2h_bytes_per_step": C_h.numel() * 4},
+                 3 * args.steps, clk, err, world,
+                 warm_l2={"ms_per_step": warm_ms, "tflops": _job_value(flop, warm_ms, world),
+                          "phases_ms": {k_: round(v_, 4) for k_, v_ in warm_per.items()}},
+                 plan_ms={"median": statistics.median(plan_s) * 1e3, "runs": len(plan_s),
+                          "what": "oversketch_plan host wall time: table allocation, hash, bucket-CSR, synchronise"})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_hessian(args):
@@ -931,7 +1110,9 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-GEMM comparison")
-    ap.add_argument("--workload", default="square", choices=["square", "hessian", "batched", "autograd", "lp", "sec51"],
+    ap.add_argument("--no-forms", action="store_true", help="square: skip timing the other GEMM dtypes")
+    ap.add_argument("--workload", default="square",
+                    choices=["square", "small", "hessian", "batched", "autograd", "lp", "sec51"],
                     help="square (default: the headline line), or another workload of the suite")
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
     ap.add_argument("--recompute", action="store_true", help="autograd: recompute the sketches in backward")
@@ -941,6 +1122,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "small":
+        return run_small(args)
     if args.workload == "hessian":
         return run_hessian(args)
     if args.workload == "batched":

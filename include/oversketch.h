@@ -228,9 +228,12 @@ OS_API os_status oversketch_sketch_left_sparse(oversketch_plan_t plan, const voi
  *   - Limit: oversketch_sketch_workspace(plan, m, a_t) <= 32 MiB (for FP32
  *     that is about ceil(m/128) * 128 * n * 4 bytes plus 4 * (N+e) * (n + 3b)
  *     bytes of entry weights), else OS_ERR_WORKSPACE and no launch.
- *   - The first call on a device looks up the scratch array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Arguments are checked as by oversketch_sketch_left, and an empty output
+ *     (m = 0) returns OS_OK, before anything else happens.
+ *   - The first call in a CUDA context looks up the scratch array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that first
+ *     call before any stream capture.  A context created later on the same
+ *     device (after cudaDeviceReset) gets its own lookup on its first call.
  *   - All calls share the array and it keeps the last call's contents; every
  *     byte a call reads is written by that call first, so nothing needs
  *     clearing.  Calls that overlap on the GPU (different streams, or several
@@ -245,11 +248,13 @@ OS_API os_status oversketch_sketch_left_noalloc(oversketch_plan_t plan, const vo
  * Masked block-sum GEMM (Alg. 3 computation + termination + reduction; the
  * b x b block products of Alg. 2 become one GEMM whose inner dimension is
  * the concatenation of the kept blocks):
- *   C[r, c] = alpha * sum_{j in mask} sum_{q < b} At[r, j*b + q] * BtT[c, j*b + q]
- *            (+ beta * C[r, c] when beta != 0)
+ *   C[r, c] = (alpha / k) * sum_{j in mask} sum_{q < b} At[r, j*b + q] * BtT[c, j*b + q]
+ *            (+ beta * C[r, c] when beta != 0),   k = popcount(mask)
+ * The 1/k of (*) is applied here, derived from the mask (the sketches are
+ * unscaled); alpha = 1 gives (*), other values scale it further.
  * At: m x z (ldat), BtT: l x z (ldbt), both in dtype `dt`; FP8 operands
  * carry the per-(row, 128-q) scales produced by the sketches.  C: FP32
- * m x l (ldc).  Pass alpha = 1/popcount(mask) for (*).  OS_F32 operands are
+ * m x l (ldc).  OS_F32 operands are
  * computed at FP32 accuracy, BF16 and FP8 on the tensor cores with FP32
  * accumulation.  K tiles: 16 (FP32), 64 (BF16), 128 (FP8); b must be a
  * multiple of the K tile.  Tensor-core operands need 16-byte aligned rows.
@@ -342,6 +347,32 @@ OS_API os_status oversketch_unsketch_rows(oversketch_plan_t plan, const float *U
                                    os_dtype g_t, int64_t ldg, void *stream);
 
 /* -------------------------------------------------------------------------
+ * Backward pass of (*) (the adjoint of Eq. 3's map S restricted to the kept
+ * blocks; C is bilinear in A and B):
+ *   dX = (1/k) (dC . B~_sel^T) . S_sel^T          (m x n, the gradient for A)
+ *   dG = (1/k) S_sel . (A~_sel^T . dC)            (n x l, the gradient for B)
+ * with k = popcount(mask), derived here from the mask.  At (m x z, ldat) and
+ * BtT (l x z, ldbt) are the BF16 sketches of the forward pass (only the kept
+ * blocks are read); dC: FP32 m x l (lddc).  Each side is one BF16 tensor-core
+ * GEMM with FP32 accumulation (dC rounded to BF16, 1/k in the GEMM epilogue)
+ * followed by an unsketch gather into dX (x_t) or dG (g_t), OS_F32 or OS_BF16.
+ * dX or dG may be NULL: that side is skipped.  workspace: device memory of
+ * oversketch_matmul_backward_workspace_size(plan, m, l, mask, dX != NULL,
+ * dG != NULL) bytes (the BF16 layouts of dC, the transposed kept blocks and the
+ * FP32 GEMM results).  Asynchronous on `stream`.
+ * Errors: OS_ERR_MASK, OS_ERR_INVALID_ARG, OS_ERR_DTYPE, OS_ERR_WORKSPACE,
+ * OS_ERR_UNSUPPORTED (see unsketch_cols), OS_ERR_CUDA.
+ */
+OS_API os_status oversketch_matmul_backward_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
+                                                           uint64_t mask, int32_t need_dx, int32_t need_dg,
+                                                           size_t *bytes);
+OS_API os_status oversketch_matmul_backward(oversketch_plan_t plan, const void *At, int64_t ldat,
+                                            const void *BtT, int64_t ldbt, const float *dC, int64_t lddc,
+                                            int64_t m, int64_t l, uint64_t mask, void *dX, os_dtype x_t,
+                                            int64_t ldx, void *dG, os_dtype g_t, int64_t ldg, void *workspace,
+                                            size_t ws_bytes, void *stream);
+
+/* -------------------------------------------------------------------------
  * Plain BF16 GEMM on the tensor cores (the same tcgen05 kernel with one K
  * block), used by the backward pass:
  *   C = alpha * A . B^T (+ beta * C),  A: m x K, B: n x K, both K-major BF16
@@ -388,6 +419,18 @@ OS_API os_status oversketch_frob(const float *X, int64_t ldx, const float *Y, in
  * clears the word.  Synchronises `stream`.
  */
 OS_API os_status oversketch_device_status(void *stream, int32_t *status, int32_t reset);
+
+/* Test hook of the bounded waits; the paper has no counterpart.  With
+ * skip_kb >= 0, the next launch of the one-CTA tensor-core GEMM (the FP8 and
+ * 3xTF32 masked products, grouped BF16 launches) leaves K step skip_kb of its
+ * first CTA's first tile unloaded and unarmed, and gives that CTA a wait limit
+ * of limit_ns (> 0) instead of one second: the MMA warp's wait for that stage
+ * runs out, the CTA records OS_ERR_TIMEOUT, waits (one second at most) for the
+ * copies it did issue, frees its tensor memory and returns.  The setting is
+ * consumed by that one launch; skip_kb < 0 withdraws a pending one.
+ * Synchronous (device-wide symbol copies).  Errors: OS_ERR_INVALID_ARG
+ * (limit_ns == 0 with skip_kb >= 0), OS_ERR_CUDA. */
+OS_API os_status oversketch_test_wait_timeout(uint64_t limit_ns, int32_t skip_kb);
 
 /* -------------------------------------------------------------------------
  * Batches of independent products (Alg. 3's blocks are independent jobs;

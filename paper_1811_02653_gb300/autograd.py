@@ -7,8 +7,9 @@ Backward: C is bilinear in (X, G) and S enters linearly (Eq. 3), so
 
     dX = (1/k) (dC . B~_sel^T) . S_sel^T     dG = (1/k) S_sel . (A~_sel^T . dC)
 
-computed as a tensor-core GEMM followed by an unsketch kernel (a signed gather
-through the hash tables; every output written once, no atomics).  The sketched
+computed by oversketch_matmul_backward: per side a tensor-core GEMM (the 1/k
+in its epilogue) followed by an unsketch kernel (a signed gather through the
+hash tables; every output written once, no atomics).  The sketched
 operands A~ = X S and B~ = S^T G are either kept from the forward pass or, with
 ``recompute=True``, recomputed from X and G (two sketch launches instead of
 holding m*z + l*z BF16 values).
@@ -20,10 +21,6 @@ from __future__ import annotations
 import torch
 
 from . import ops
-
-
-def _k(mask: int) -> int:
-    return bin(mask).count("1")
 
 
 class OverSketchMatmul(torch.autograd.Function):
@@ -57,20 +54,10 @@ class OverSketchMatmul(torch.autograd.Function):
             BtT, _ = ops.sketch_right(plan, G, "bf16", block_mask=mask)
         else:
             At, BtT = ctx.saved_tensors
-        k, b = _k(mask), plan.b
         if dC.stride(-1) != 1:
             dC = dC.contiguous()
-        dX = dG = None
-        if ctx.needs_input_grad[0]:
-            dC16 = ops.cast(dC, "bf16")                                   # m x l
-            Bsel = ops.select_transpose(BtT, "bf16", block_mask=mask, b=b)  # (k b) x l
-            T = ops.gemm_bf16(dC16, Bsel, alpha=1.0 / k)                 # m x (k b)
-            dX = ops.unsketch_cols(plan, T, mask, 1.0, out_dtype=ctx.x_dtype)
-        if ctx.needs_input_grad[1]:
-            Aselt = ops.select_transpose(At, "bf16", block_mask=mask, b=b)  # (k b) x m
-            dCt16 = ops.select_transpose(dC, "bf16")                     # l x m
-            U = ops.gemm_bf16(Aselt, dCt16, alpha=1.0 / k)               # (k b) x l
-            dG = ops.unsketch_rows(plan, U, mask, 1.0, out_dtype=ctx.g_dtype)
+        dX, dG = ops.matmul_backward(plan, At, BtT, dC.float(), mask, ctx.x_dtype, ctx.g_dtype,
+                                     need_dx=ctx.needs_input_grad[0], need_dg=ctx.needs_input_grad[1])
         return dX, dG, None, None, None
 
 

@@ -177,14 +177,16 @@ extern "C" os_status oversketch_gemm_masked(oversketch_plan_t plan, const void *
     const int64_t z = (int64_t)p->P * p->b;
     if (ldat < z || ldbt < z) return OS_ERR_INVALID_ARG;
     cudaStream_t st = as_stream(stream);
+    // the 1/k of (*) (Eq. 3's 1/sqrt(N) on both sides, k = N under Alg. 3's rule)
+    const float scale = alpha / (float)__builtin_popcountll(mask);
     switch (dt) {
         case OS_F32:
             return gemm_masked_f32(p, (const float *)At, ldat, (const float *)BtT, ldbt, m, l, mask,
-                                   alpha, beta, C, ldc, st);
+                                   scale, beta, C, ldc, st);
         case OS_BF16:
         case OS_FP8E4M3:
         case OS_TF32X2:
-            return gemm_masked_tc(p, At, ldat, a_scales, BtT, ldbt, b_scales, dt, m, l, mask, alpha,
+            return gemm_masked_tc(p, At, ldat, a_scales, BtT, ldbt, b_scales, dt, m, l, mask, scale,
                                   beta, C, ldc, st);
     }
     return OS_ERR_DTYPE;
@@ -235,10 +237,8 @@ extern "C" os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os
     else
         OSK_TRY(sketch_left_impl(p, A, a_t, m, lda, At, g, L.ldat, as, cs, mask, lws, L.left_ws, st));
     if (!sym) OSK_TRY(sketch_right_impl(p, B, b_t, l, ldb, BtT, g, L.ldbt, bs, mask, lws, L.left_ws, st));
-    int k = 0;
-    for (int j = 0; j < p->P; ++j) k += (int)((mask >> j) & 1ull);
-    return oversketch_gemm_masked(plan, At, L.ldat, as, BtT, L.ldbt, bs, g, m, l, mask, 1.0f / (float)k,
-                                  0.0f, C, ldc, stream);
+    return oversketch_gemm_masked(plan, At, L.ldat, as, BtT, L.ldbt, bs, g, m, l, mask, 1.0f, 0.0f, C, ldc,
+                                  stream);
 }
 
 extern "C" os_status oversketch_frob(const float *X, int64_t ldx, const float *Y, int64_t ldy,
@@ -428,14 +428,12 @@ extern "C" os_status oversketch_matmul_host(oversketch_plan_t plan, const void *
         }
         if (st != OS_OK) break;
         // the GEMM in row panels; each panel of C goes back while the next is computed
-        int k = 0;
-        for (int j = 0; j < p->P; ++j) k += (int)((mask >> j) & 1ull);
         for (int64_t q = 0; q < npanels; ++q) {
             const int64_t r0 = q * h.c_rows, rows = (m - r0 < h.c_rows) ? m - r0 : h.c_rows;
             const void *at_q = (const char *)At + (size_t)r0 * L.ldat * dtype_size(g);
             const float *as_q = as ? as + r0 : nullptr;   // slice-major scales: the panel's rows start at r0
-            if ((st = oversketch_gemm_masked(plan, at_q, L.ldat, as_q, BtT, L.ldbt, bs, g, rows, l, mask,
-                                             1.0f / (float)k, 0.0f, Cd + r0 * h.ldc_d, h.ldc_d, cs)) != OS_OK)
+            if ((st = oversketch_gemm_masked(plan, at_q, L.ldat, as_q, BtT, L.ldbt, bs, g, rows, l, mask, 1.0f,
+                                             0.0f, Cd + r0 * h.ldc_d, h.ldc_d, cs)) != OS_OK)
                 break;
             cudaEvent_t ec;
             if ((st = event(&ec)) != OS_OK) break;
@@ -455,6 +453,105 @@ extern "C" os_status oversketch_matmul_host(oversketch_plan_t plan, const void *
     } while (0);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);   // released once their work completes
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Backward pass of (*) as a function of both operands (the adjoint of Eq. 3's
+// linear map S restricted to the kept blocks):
+//   dX = (1/k) (dC . B~_sel^T) . S_sel^T      dG = (1/k) S_sel . (A~_sel^T . dC)
+// Each side is a BF16 tensor-core GEMM with FP32 accumulation (the 1/k applied in
+// its epilogue) followed by an unsketch gather; the operand layouts the GEMMs need
+// (dC in BF16, the kept blocks of B~^T and A~ transposed, dC^T) are written into
+// the workspace first.
+namespace osk {
+namespace {
+
+struct BackwardLayout {
+    int64_t kb, ld_l, ld_m, ld_kb;   // padded row pitches (elements) of the BF16 / FP32 buffers
+    size_t dc16, bsel, t, asel, dct16, u;
+};
+
+BackwardLayout backward_layout(const Plan *p, int64_t m, int64_t l, uint64_t mask) {
+    BackwardLayout L;
+    L.kb = (int64_t)__builtin_popcountll(mask) * p->b;
+    L.ld_l = (l + 7) / 8 * 8;      // BF16 rows of l elements, 16-byte aligned
+    L.ld_m = (m + 7) / 8 * 8;      // BF16 rows of m elements
+    L.ld_kb = (L.kb + 3) / 4 * 4;  // FP32 rows of k*b elements
+    L.dc16 = align256((size_t)m * L.ld_l * 2);
+    L.bsel = align256((size_t)L.kb * L.ld_l * 2);
+    L.t = align256((size_t)m * L.ld_kb * 4);
+    L.asel = align256((size_t)L.kb * L.ld_m * 2);
+    L.dct16 = align256((size_t)l * L.ld_m * 2);
+    L.u = align256((size_t)L.kb * ((l + 3) / 4 * 4) * 4);
+    return L;
+}
+
+size_t backward_bytes(const BackwardLayout &L, bool need_dx, bool need_dg) {
+    return (need_dx ? L.dc16 + L.bsel + L.t : 0) + (need_dg ? L.asel + L.dct16 + L.u : 0) + 256;
+}
+
+}  // namespace
+}  // namespace osk
+
+extern "C" os_status oversketch_matmul_backward_workspace_size(oversketch_plan_t plan, int64_t m, int64_t l,
+                                                                uint64_t mask, int32_t need_dx, int32_t need_dg,
+                                                                size_t *bytes) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p || !bytes || m < 0 || l < 0) return OS_ERR_INVALID_ARG;
+    OSK_TRY(check_mask(mask, p->P));
+    *bytes = backward_bytes(backward_layout(p, m, l, mask), need_dx != 0, need_dg != 0);
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_matmul_backward(oversketch_plan_t plan, const void *At, int64_t ldat,
+                                                const void *BtT, int64_t ldbt, const float *dC, int64_t lddc,
+                                                int64_t m, int64_t l, uint64_t mask, void *dX, os_dtype x_t,
+                                                int64_t ldx, void *dG, os_dtype g_t, int64_t ldg, void *workspace,
+                                                size_t ws_bytes, void *stream) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p || m < 0 || l < 0 || lddc < l) return OS_ERR_INVALID_ARG;
+    OSK_TRY(check_mask(mask, p->P));
+    const int64_t z = (int64_t)p->P * p->b;
+    if ((dX && (x_t != OS_F32 && x_t != OS_BF16)) || (dG && (g_t != OS_F32 && g_t != OS_BF16))) return OS_ERR_DTYPE;
+    if ((dX && (ldbt < z || ldx < p->n)) || (dG && (ldat < z || ldg < l))) return OS_ERR_INVALID_ARG;
+    const bool need_dx = dX != nullptr && m > 0, need_dg = dG != nullptr && l > 0;
+    if (!need_dx && !need_dg) return OS_OK;
+    const BackwardLayout L = backward_layout(p, m, l, mask);
+    if (!workspace || ws_bytes < backward_bytes(L, need_dx, need_dg)) return OS_ERR_WORKSPACE;
+    if (!dC && m > 0 && l > 0) return OS_ERR_INVALID_ARG;
+    const float inv_k = 1.0f / (float)__builtin_popcountll(mask);
+    char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
+    if (need_dx) {
+        if (l > 0 && !BtT) return OS_ERR_INVALID_ARG;
+        void *dc16 = base;
+        void *bsel = base + L.dc16;
+        float *T = reinterpret_cast<float *>(base + L.dc16 + L.bsel);
+        base += L.dc16 + L.bsel + L.t;
+        if (l > 0) {
+            OSK_TRY(oversketch_cast(dC, OS_F32, m, l, lddc, dc16, OS_BF16, L.ld_l, stream));
+            OSK_TRY(oversketch_select_transpose(BtT, OS_BF16, l, z, ldbt, mask, p->b, bsel, OS_BF16, L.ld_l, stream));
+            OSK_TRY(oversketch_gemm_bf16(dc16, L.ld_l, bsel, L.ld_l, m, L.kb, l, inv_k, 0.0f, T, L.ld_kb, stream));
+        } else {
+            OSK_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)m * L.ld_kb * 4, as_stream(stream)));
+        }
+        OSK_TRY(oversketch_unsketch_cols(plan, T, m, L.ld_kb, mask, 1.0f, dX, x_t, ldx, stream));
+    }
+    if (need_dg) {
+        if (m > 0 && !At) return OS_ERR_INVALID_ARG;
+        void *asel = base;
+        void *dct16 = base + L.asel;
+        float *U = reinterpret_cast<float *>(base + L.asel + L.dct16);
+        const int64_t ldu = (l + 3) / 4 * 4;
+        if (m > 0) {
+            OSK_TRY(oversketch_select_transpose(At, OS_BF16, m, z, ldat, mask, p->b, asel, OS_BF16, L.ld_m, stream));
+            OSK_TRY(oversketch_select_transpose(dC, OS_F32, m, l, lddc, 0, 0, dct16, OS_BF16, L.ld_m, stream));
+            OSK_TRY(oversketch_gemm_bf16(asel, L.ld_m, dct16, L.ld_m, L.kb, l, m, inv_k, 0.0f, U, ldu, stream));
+        } else {
+            OSK_CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)L.kb * ldu * 4, as_stream(stream)));
+        }
+        OSK_TRY(oversketch_unsketch_rows(plan, U, l, ldu, mask, 1.0f, dG, g_t, ldg, stream));
+    }
+    return OS_OK;
 }
 
 // Sketch size for a target accuracy (Thm. 4.1): d = 2/(eps*theta) columns make

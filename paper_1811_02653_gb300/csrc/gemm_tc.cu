@@ -182,6 +182,10 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
     uint64_t *sf_ready = drain + 1;    // FP8: stage's scale chunks written (STAGES barriers)
     uint32_t *tmem_base_slot = reinterpret_cast<uint32_t *>(sf_ready + STAGES);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_base_slot + 1);
+    // test hook (first CTA only): a K step of the first tile left unloaded, and this
+    // CTA's wait limit
+    __shared__ int s_skip_kb;
+    __shared__ unsigned long long s_wait_ns;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -199,6 +203,12 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
         mbar_init(drain, 1);
         for (int s = 0; s < STAGES; ++s) mbar_init(&sf_ready[s], 1);
         *abort = 0;
+        s_skip_kb = -1;
+        s_wait_ns = kWaitLimitNs;
+        if (blockIdx.x == 0 && *(volatile int *)&g_test_skip_kb >= 0) {
+            s_skip_kb = atomicExch(&g_test_skip_kb, -1);   // one-shot
+            s_wait_ns = *(volatile unsigned long long *)&g_test_wait_ns;
+        }
         fence_barrier_init();
         if constexpr (!GROUPED) {
             prefetch_tmap(&tmap_a0);
@@ -214,6 +224,8 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_base_slot;
+    const int skip_kb = s_skip_kb;
+    const unsigned long long wait_ns = s_wait_ns;
 
     // The tile's product, coordinates and epilogue parameters.
     auto job = [&](int t) {
@@ -268,7 +280,13 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
                 const TileJob j = job(t);
                 for (int kb = 0; kb < j.num_kb; ++kb) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort)) { ok = false; break; }
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, abort, wait_ns)) { ok = false; break; }
+                    if (t == blockIdx.x && kb == skip_kb) {
+                        // test hook: this stage is never loaded nor armed, so the
+                        // MMA warp's wait for it runs out
+                        if (++stage == STAGES) stage = 0, phase ^= 1u;
+                        continue;
+                    }
                     const int blk = kb / j.kb_per_blk;
                     const int kidx = GROUPED ? j.kept[blk] : g.kept.idx[blk];
                     const int kz = kidx * j.b + (kb - blk * j.kb_per_blk) * BKE;
@@ -306,14 +324,14 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             const int kc_end = min(num_kb, kc + C::CHUNK_KB);
             const int a = iter & 1;
             const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
-            if (!__all_sync(0xffffffffu, mbar_wait(&tmem_empty[a], aphase ^ 1u, abort))) { ok = false; break; }
+            if (!__all_sync(0xffffffffu, mbar_wait(&tmem_empty[a], aphase ^ 1u, abort, wait_ns))) { ok = false; break; }
             tc_fence_after();
             const uint32_t d = tmem_base + (uint32_t)(a * C::ACC_STRIDE);
             for (int kb = kc; kb < kc_end; ++kb) {
                 // FP8: the converter warp signals sf_ready once the stage's tiles have
                 // landed and its scale chunks are written
                 uint64_t *ready = C::FP8 ? &sf_ready[stage] : &full[stage];
-                if (!__all_sync(0xffffffffu, mbar_wait(ready, phase, abort))) { ok = false; break; }
+                if (!__all_sync(0xffffffffu, mbar_wait(ready, phase, abort, wait_ns))) { ok = false; break; }
                 tc_fence_after();
                 uint8_t *st = tiles + stage * C::STAGE_BYTES;
                 const uint32_t sa0 = smem_u32(st);
@@ -373,7 +391,7 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
                 const int num_kb = num_kb_of(t);
                 for (int kb = 0; kb < num_kb; ++kb) {
-                    if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, abort))) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(&full[stage], phase, abort, wait_ns))) { ok = false; break; }
                     uint8_t *st = tiles + stage * C::STAGE_BYTES;
                     const float *fa = reinterpret_cast<const float *>(st + C::TILE_BYTES);
                     const float *fb = fa + BM;
@@ -447,7 +465,7 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                     const int a = iter & 1;
                     const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
                     // warp-uniform decision: tcgen05.ld below is a .sync.aligned instruction
-                    if (!__all_sync(0xffffffffu, mbar_wait(&tmem_full[a], aphase, abort))) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(&tmem_full[a], aphase, abort, wait_ns))) { ok = false; break; }
                     tc_fence_after();
 #pragma unroll
                     for (int ch = 0; ch < BN / 32; ++ch) {
@@ -467,7 +485,7 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                 const int a = iter & 1;
                 const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
                 ++iter;
-                if (!__all_sync(0xffffffffu, mbar_wait(&tmem_full[a], aphase, abort))) break;
+                if (!__all_sync(0xffffffffu, mbar_wait(&tmem_full[a], aphase, abort, wait_ns))) break;
                 tc_fence_after();
                 for (int ch = 0; ch < BN / 32; ++ch) {
                     uint32_t v[32];
@@ -1016,6 +1034,15 @@ extern "C" os_status oversketch_device_status(void *stream, int32_t *status, int
         OSK_CUDA_TRY(cudaMemcpyToSymbolAsync(tc::g_device_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st));
         OSK_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_test_wait_timeout(uint64_t limit_ns, int32_t skip_kb) {
+    if (skip_kb >= 0 && limit_ns == 0) return OS_ERR_INVALID_ARG;
+    const unsigned long long lim = skip_kb >= 0 ? (unsigned long long)limit_ns : tc::kWaitLimitNs;
+    const int skip = skip_kb >= 0 ? skip_kb : -1;
+    OSK_CUDA_TRY(cudaMemcpyToSymbol(tc::g_test_wait_ns, &lim, sizeof(lim)));
+    OSK_CUDA_TRY(cudaMemcpyToSymbol(tc::g_test_skip_kb, &skip, sizeof(skip)));
     return OS_OK;
 }
 

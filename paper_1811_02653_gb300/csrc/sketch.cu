@@ -730,10 +730,10 @@ os_status make_weights(const Plan *p, const float *s, uint64_t block_mask, float
 }
 }  // namespace
 
-os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
-                           void *At, os_dtype out_t, int64_t ldat, float *scales,
-                           const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
-                           cudaStream_t st) {
+// The argument checks of the left sketch that need no workspace (OS_OK for a
+// valid call, including an empty output m == 0).
+os_status sketch_left_check(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda, void *At,
+                            os_dtype out_t, int64_t ldat, float *scales, uint64_t block_mask) {
     if (!p || m < 0) return OS_ERR_INVALID_ARG;
     if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (a_t != OS_F32 && a_t != OS_BF16) return OS_ERR_DTYPE;
@@ -741,6 +741,15 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
     OSK_TRY(check_out(p, m, At, out_t, ldat, scales));
     if (m == 0) return OS_OK;
     if (!A) return OS_ERR_INVALID_ARG;
+    return OS_OK;
+}
+
+os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
+                           void *At, os_dtype out_t, int64_t ldat, float *scales,
+                           const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    OSK_TRY(sketch_left_check(p, A, a_t, m, lda, At, out_t, ldat, scales, block_mask));
+    if (m == 0) return OS_OK;
     if (!ws || ws_bytes < sketch_workspace_bytes(p, m, a_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);
     const float *wts = nullptr;

@@ -17,6 +17,13 @@ __device__ unsigned int g_device_status;
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s per wait
 
+// Test hook of the bounded waits (oversketch_test_wait_timeout): when >= 0, the
+// next launch of gemm_masked_tc_kernel takes this value (one-shot) and its first
+// CTA leaves that K step of its first tile unloaded, with g_test_wait_ns as the
+// CTA's wait limit, so that the wait for that stage runs out.
+__device__ int g_test_skip_kb = -1;
+__device__ unsigned long long g_test_wait_ns = kWaitLimitNs;
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -57,15 +64,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Wait for the phase of parity `parity` to complete.  Gives up (returns false)
-// after kWaitLimitNs, or early when another role of the CTA raised *abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+// after limit_ns, or early when another role of the CTA raised *abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0) {
             if (*abort) return false;
-            if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            if (globaltimer_ns() - t0 > limit_ns) {
                 *abort = 1;
                 atomicOr(&g_device_status, 1u);
                 return false;

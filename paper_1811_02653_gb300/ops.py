@@ -108,6 +108,10 @@ def load_library(path: str | None = None):
             "oversketch_batch_run": (st, [vp, vp]),
             "oversketch_batch_info": (st, [vp, ctypes.POINTER(_BatchInfo)]),
             "oversketch_batch_destroy": (st, [vp]),
+            "oversketch_test_wait_timeout": (st, [u64, i32]),
+            "oversketch_matmul_backward_workspace_size": (st, [vp, i64, i64, u64, i32, i32, ctypes.POINTER(sz)]),
+            "oversketch_matmul_backward": (st, [vp, vp, i64, vp, i64, vp, i64, i64, i64, u64, vp, st, i64, vp, st,
+                                                i64, vp, sz, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -132,7 +136,8 @@ def _sigs_names():
             "oversketch_batch_create", "oversketch_batch_run", "oversketch_batch_info",
             "oversketch_batch_destroy", "oversketch_sketch_left_sparse",
             "oversketch_matmul_host_workspace_size", "oversketch_matmul_host", "oversketch_sketch_size",
-            "oversketch_gemm_masked_blocks"]
+            "oversketch_gemm_masked_blocks", "oversketch_matmul_backward_workspace_size", "oversketch_test_wait_timeout",
+            "oversketch_matmul_backward"]
 
 
 def _check(status: int, what: str):
@@ -353,13 +358,12 @@ def sketch_right(p: Plan, B: torch.Tensor, out_dtype="f32", out=None, scales=Non
     return out, scales
 
 
-def gemm_masked(p: Plan, At, BtT, mask: int, alpha=None, beta=0.0, C=None, a_scales=None,
+def gemm_masked(p: Plan, At, BtT, mask: int, alpha=1.0, beta=0.0, C=None, a_scales=None,
                 b_scales=None, dtype=None, stream=None):
-    """C = alpha * sum_{j in mask} At_j BtT_j^T (+ beta C); alpha defaults to 1/k.
+    """C = (alpha/k) * sum_{j in mask} At_j BtT_j^T (+ beta C), k = popcount(mask)
+    applied by the library (alpha = 1: the OverSketch product).
     ``dtype`` overrides the operand dtype (e.g. "tf32x2" for hi/lo planes)."""
     m, l = At.shape[0], BtT.shape[0]
-    if alpha is None:
-        alpha = 1.0 / bin(mask).count("1")
     if C is None:
         C = torch.empty((m, l), dtype=torch.float32, device=At.device)
     _check(load_library().oversketch_gemm_masked(
@@ -458,6 +462,34 @@ def matmul_host(p: Plan, A, B, mask: int, gemm_dtype="f32", C=None, col_scale=No
     return C
 
 
+def matmul_backward_workspace(p: Plan, m: int, l: int, mask: int, need_dx=True, need_dg=True) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().oversketch_matmul_backward_workspace_size(p.handle, m, l, mask, 1 if need_dx else 0,
+                                                                    1 if need_dg else 0, ctypes.byref(out)),
+           "oversketch_matmul_backward_workspace_size")
+    return out.value
+
+
+def matmul_backward(p: Plan, At, BtT, dC, mask: int, x_dtype=torch.float32, g_dtype=torch.float32,
+                    need_dx=True, need_dg=True, workspace=None, stream=None):
+    """(dX, dG) of C = (1/k)(A S_sel)(S_sel^T B) for the upstream gradient dC (FP32
+    m x l), from the forward pass's BF16 sketches At (m x z) and BtT (l x z);
+    the library applies 1/k.  A side not needed comes back as None."""
+    m, l = dC.shape
+    lddc = _rowmajor(dC, "dC")
+    dX = torch.empty((m, p.n), dtype=x_dtype, device=dC.device) if need_dx else None
+    dG = torch.empty((p.n, l), dtype=g_dtype, device=dC.device) if need_dg else None
+    if workspace is None:
+        workspace = torch.empty(matmul_backward_workspace(p, m, l, mask, need_dx, need_dg), dtype=torch.uint8,
+                                device=dC.device)
+    _check(load_library().oversketch_matmul_backward(
+        p.handle, _ptr(At), At.stride(0) if At is not None else 0, _ptr(BtT), BtT.stride(0) if BtT is not None else 0,
+        _ptr(dC), lddc, m, l, mask, _ptr(dX), _dt(dX) if dX is not None else F32, dX.stride(0) if dX is not None else 0,
+        _ptr(dG), _dt(dG) if dG is not None else F32, dG.stride(0) if dG is not None else 0, _ptr(workspace),
+        workspace.numel(), _stream(stream)), "oversketch_matmul_backward")
+    return dX, dG
+
+
 def unsketch_cols(p: Plan, T, mask: int, scale: float, out_dtype="f32", out=None, stream=None):
     m = T.shape[0]
     od = _dtype_code(out_dtype)
@@ -496,6 +528,12 @@ def device_status(reset=True, stream=None) -> int:
     _check(load_library().oversketch_device_status(_stream(stream), ctypes.byref(out), 1 if reset else 0),
            "oversketch_device_status")
     return out.value
+
+
+def test_wait_timeout(limit_ns: int, skip_kb: int):
+    """Test hook: the next one-CTA tensor-core GEMM launch leaves K step skip_kb of
+    its first tile unloaded and gives up after limit_ns (skip_kb < 0 withdraws it)."""
+    _check(load_library().oversketch_test_wait_timeout(limit_ns, skip_kb), "oversketch_test_wait_timeout")
 
 
 def sketch_left_noalloc(p: Plan, A: torch.Tensor, out: torch.Tensor, out_dtype="f32", col_scale=None,

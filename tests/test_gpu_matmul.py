@@ -79,7 +79,7 @@ def test_gemm_masked_beta_and_alpha(ops):
     p = ops.plan(n, b, N, e, 0)
     C = _dev(C0.copy())
     ops.gemm_masked(p, _dev(At), _dev(BtT), 0b1101, alpha=0.5, beta=2.0, C=C)
-    ref = 0.5 * 3 * oracle.masked_product(At, BtT.T, b, 0b1101) + 2.0 * C0
+    ref = 0.5 * oracle.masked_product(At, BtT.T, b, 0b1101) + 2.0 * C0          # the library's 1/k, times alpha
     assert oracle.rel_frob(C.cpu().numpy(), ref) <= 1e-6
 
 
@@ -94,25 +94,57 @@ def test_matmul_mask_errors(ops):
         ops.matmul(p, torch.zeros((8, 500), device="cuda"), B, 0b111, "f32")   # n mismatch
 
 
-def test_square_workload_sampled_fp32(ops):
-    # full-size square workload (16384 x 65536 x 16384), FP32 path, checked on
-    # sampled rows and columns that the oracle computes one by one
+@pytest.fixture(scope="module")
+def square(ops):
+    """The full-size square workload (16384 x 65536 x 16384, FP32 operands with
+    the rank-64 spike) on the device, with sampled rows of A and columns of B
+    that the oracle regenerates one by one, and their oracle sketches."""
     w = W.SQUARE
     A = torch.from_numpy(w.left()).cuda()
     Bt_host = w.right_cols(range(w.l))                       # l x n (columns of B)
     B = torch.from_numpy(Bt_host).cuda().t().contiguous()
     del Bt_host
     p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
-    C = ops.matmul(p, A, B, w.mask, "f32")
-    torch.cuda.synchronize()
-    rows = [0, 1, 777, 8191, 16383]
+    rows = [0, 1, 777, 8191, 12288, 16383]
     cols = [0, 5, 4096, 12345, 16383]
     h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
-    Ar = w.left_rows(rows)
-    Bc = w.right_cols(cols).T
-    C_ref = oracle.oversketch(Ar, Bc, h, s, w.b, w.mask)
+    At64 = oracle.sketch_left(w.left_rows(rows), h, s, w.b)          # FP64 sketches of the samples
+    Bt64 = oracle.sketch_right(w.right_cols(cols).T, h, s, w.b)
+    yield w, A, B, p, rows, cols, At64, Bt64
+    del A, B
+
+
+def test_square_workload_sampled_fp32(ops, square):
+    # full-size square workload, FP32 path (3xTF32 GEMM), sampled rows and columns
+    w, A, B, p, rows, cols, At64, Bt64 = square
+    C = ops.matmul(p, A, B, w.mask, "f32")
     C_s = C[rows][:, cols].cpu().numpy()
-    assert oracle.rel_frob(C_s, C_ref) <= 1e-5
+    assert oracle.rel_frob(C_s, oracle.masked_product(At64, Bt64, w.b, w.mask)) <= 1e-5
+
+
+def test_square_workload_sampled_bf16(ops, square):
+    # the headline form: BF16 sketches (RNE of the FP32 sums) and the CTA-pair
+    # tcgen05 GEMM; the oracle rounds its FP64 sketches to BF16 the same way
+    w, A, B, p, rows, cols, At64, Bt64 = square
+    C = ops.matmul(p, A, B, w.mask, "bf16")
+    C_s = C[rows][:, cols].cpu().numpy()
+    ref = oracle.masked_product(oracle.round_bf16(At64), oracle.round_bf16(Bt64), w.b, w.mask)
+    assert oracle.rel_frob(C_s, ref) <= 1e-4
+    assert ops.device_status() == 0
+
+
+def test_square_workload_sampled_fp8(ops, square):
+    # FP8 E4M3 sketches with per-(row, 128-column) UE8M0 scales and the
+    # block-scaled tcgen05 GEMM; the oracle quantises its FP64 sketch rows with
+    # the same scale rule
+    w, A, B, p, rows, cols, At64, Bt64 = square
+    C = ops.matmul(p, A, B, w.mask, "fp8")
+    C_s = C[rows][:, cols].cpu().numpy()
+    Aq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(At64))
+    Bq = oracle.dequantize_fp8_rows(*oracle.quantize_fp8_rows(Bt64.T))
+    ref = oracle.masked_product(Aq, Bq.T, w.b, w.mask)
+    assert oracle.rel_frob(C_s, ref) <= 1e-3
+    assert ops.device_status() == 0
 
 
 def test_empty_operands(ops):
