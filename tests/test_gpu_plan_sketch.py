@@ -108,6 +108,42 @@ def test_sketch_fp32_parity(ops, m, n, l, b, N, e):
     assert torch.equal(At, At2)
 
 
+@pytest.mark.parametrize("m,n,b,N,e,in_dtype,scaled,out", [
+    (1000, 20_000, 256, 3, 1, None, False, "f32"),           # 8 strips, the last one ragged
+    (1300, 9_000, 128, 4, 1, torch.bfloat16, False, "f32"),  # BF16 input: 256-row strips, 6 strips
+    (777, 12_345, 512, 2, 2, None, True, "bf16"),            # column scale, BF16 output, ragged strip
+    (2048, 4_096, 1024, 2, 1, None, False, "tf32x2"),        # 16 strips, hi/lo planes
+])
+def test_left_sketch_many_strips(ops, m, n, b, N, e, in_dtype, scaled, out):
+    # many packed strips (128 rows of FP32, 256 of BF16), a ragged last strip, a
+    # column scale and every output form: every kept element within the FP32
+    # bound of the oracle
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    Ad = _dev(A, in_dtype)
+    A64 = Ad.float().cpu().numpy()
+    cs = rng.uniform(0.25, 4.0, n).astype(np.float32) if scaled else None
+    p = ops.plan(n, b, N, e, 3)
+    h, s = oracle.hash_tables(n, b, N, e, 3)
+    mask = (1 << (N + e)) - 1 - 2            # block 1 dropped: only the other blocks are sketched
+    At, _ = ops.sketch_left(p, Ad, out, col_scale=_dev(cs) if scaled else None, block_mask=mask)
+    ref, bd = sketch_bounds_left(A64, h, s, b, cs)
+    cols = oracle.selected_columns(mask, N + e, b)
+    if out == "tf32x2":
+        hi, lo = ops.tf32_planes(At)
+        got = hi.cpu().numpy().astype(np.float64) + lo.cpu().numpy().astype(np.float64)
+        assert_fp32_within(got[:, cols], ref[:, cols], bd[:, cols])
+    elif out == "bf16":
+        assert_bf16_within(At.float().cpu().numpy()[:, cols], ref[:, cols], bd[:, cols])
+    else:
+        assert_fp32_within(At.cpu().numpy()[:, cols], ref[:, cols], bd[:, cols])
+    At2, _ = ops.sketch_left(p, Ad, out, col_scale=_dev(cs) if scaled else None, block_mask=mask)
+    ct = torch.from_numpy(cols).cuda()
+    assert torch.equal(At[:, ct], At2[:, ct])   # bitwise reproducible (dropped blocks are left unwritten)
+    if out == "tf32x2":
+        assert torch.equal(ops.tf32_planes(At)[1][:, ct], ops.tf32_planes(At2)[1][:, ct])
+
+
 def test_sketch_col_scale(ops):
     m, n, b, N, e = 64, 3000, 256, 3, 1
     rng = np.random.default_rng(3)
