@@ -433,6 +433,47 @@ OS_API os_status oversketch_device_status(void *stream, int32_t *status, int32_t
 OS_API os_status oversketch_test_wait_timeout(uint64_t limit_ns, int32_t skip_kb);
 
 /* -------------------------------------------------------------------------
+ * Many independent products in one call, each with its own plan, sizes and kept
+ * blocks (Alg. 3: a product's block products are independent jobs, and so are
+ * whole products), its mask read from DEVICE memory when the work runs:
+ *   C_p = (1/k_p) (A_p S_p,sel)(S_p,sel^T B_p),  k_p = popcount(masks[p] & (2^P_p - 1)),
+ * so one captured CUDA graph of the call serves a different straggler set on
+ * every replay (the caller rewrites masks[] between replays).  An empty mask
+ * gives C_p = 0; bits >= N_p + e_p are ignored.
+ *   plans, A, B, C, m, n, l: HOST arrays of count (1 .. 1024) entries; A_p (m_p x
+ *     n_p, row-major, leading dim n_p) and B_p (n_p x l_p, leading dim l_p) in
+ *     a_t / b_t (OS_F32 or OS_BF16), C_p FP32 m_p x l_p (leading dim l_p), all
+ *     device memory; n_p equals the plan's n, every plan on the current device
+ *     with b % 64 == 0.  m_p = 0 or l_p = 0: product p is skipped (its pointers
+ *     may be NULL).
+ *   masks: DEVICE array of count uint64 words.
+ *   opts: NULL or gemm_dtype OS_BF16 (the GEMM runs in BF16 with FP32
+ *     accumulation); col_scale, symmetric and flags are not supported here.
+ *   workspace: device memory of oversketch_matmul_batched_workspace_size bytes:
+ *     the GEMM descriptors, every product's BF16 sketches ((m_p + l_p) z_p
+ *     elements) and eight packing slots.  The call allocates nothing: the
+ *     descriptors are written into the workspace by kernels that carry them as
+ *     launch parameters, so a captured graph holds everything it needs.
+ * Work: the descriptors, then the sketches on eight streams forked from `stream`
+ * (every block is sketched; CTAs of blocks the device mask drops return at
+ * once), then one persistent tcgen05 launch over the tiles of all products
+ * (longest sketch first), joined back on `stream`.  The sketch streams and
+ * their events belong to the library, one set per device, created on the first
+ * call (make it before any capture); calls from several host threads are
+ * enqueued one at a time.
+ * Errors: OS_ERR_INVALID_ARG, OS_ERR_DTYPE, OS_ERR_UNSUPPORTED, OS_ERR_WORKSPACE,
+ * OS_ERR_CUDA.
+ */
+OS_API os_status oversketch_matmul_batched_workspace_size(int32_t count, const oversketch_plan_t *plans,
+                                                          const int64_t *m, const int64_t *n, const int64_t *l,
+                                                          os_dtype a_t, os_dtype b_t, const os_opts *opts,
+                                                          size_t *bytes);
+OS_API os_status oversketch_matmul_batched(int32_t count, const oversketch_plan_t *plans, const void *const *A,
+                                           const void *const *B, float *const *C, const int64_t *m, const int64_t *n,
+                                           const int64_t *l, os_dtype a_t, os_dtype b_t, const uint64_t *masks,
+                                           const os_opts *opts, void *workspace, size_t ws_bytes, void *stream);
+
+/* -------------------------------------------------------------------------
  * Batches of independent products (Alg. 3's blocks are independent jobs;
  * here so are whole products).  Product p is
  *   C_p = (1/k_p) (A_p S_p,sel)(S_p,sel^T B_p),  k_p = popcount(mask_p),

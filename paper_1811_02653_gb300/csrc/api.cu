@@ -14,10 +14,11 @@ size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t);
 os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
                            const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
-                           cudaStream_t st);
+                           cudaStream_t st, const uint64_t *dmask = nullptr);
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
                             void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
-                            void *ws, size_t ws_bytes, cudaStream_t st, const float *row_scale = nullptr);
+                            void *ws, size_t ws_bytes, cudaStream_t st, const float *row_scale = nullptr,
+                            const uint64_t *dmask = nullptr);
 bool sketch_left_sparse_fits(const Plan *p, uint64_t block_mask);
 os_status sketch_left_sparse_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda, void *At,
                                   os_dtype out_t, int64_t ldat, float *scales, const float *col_scale,

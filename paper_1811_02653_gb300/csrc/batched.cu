@@ -18,6 +18,7 @@
 // and keep the fastest graph.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -28,10 +29,12 @@ namespace osk {
 
 os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda, void *At,
                            os_dtype out_t, int64_t ldat, float *scales, const float *col_scale,
-                           uint64_t block_mask, void *ws, size_t ws_bytes, cudaStream_t st);
+                           uint64_t block_mask, void *ws, size_t ws_bytes, cudaStream_t st,
+                           const uint64_t *dmask = nullptr);
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb, void *BtT,
                             os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask, void *ws,
-                            size_t ws_bytes, cudaStream_t st, const float *row_scale = nullptr);
+                            size_t ws_bytes, cudaStream_t st, const float *row_scale = nullptr,
+                            const uint64_t *dmask = nullptr);
 size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t);
 
 namespace {
@@ -100,8 +103,8 @@ os_status build_group(Batch &B, GroupTile tile) {
         const os_problem &pr = B.probs[i];
         const Plan *p = reinterpret_cast<const Plan *>(pr.plan);
         const int k = __builtin_popcountll(pr.mask);
-        OSK_TRY(group_problem_bf16(&h[q], tile, B.at[i], B.z[i], B.bt[i], B.z[i], pr.m, pr.l, B.z[i], p->b,
-                                   mask_to_list(pr.mask, p->P), 1.f / (float)k, 0.f, pr.C, pr.ldc));
+        OSK_TRY(group_problem_bf16(&h[q], tile, B.at[i], B.z[i], B.bt[i], B.z[i], pr.m, pr.l, B.z[i], p->b, p->P,
+                                   pr.mask, nullptr, 1.f / (float)k, 0.f, pr.C, pr.ldc));
         h[q].tile_begin = tiles;
         const int64_t t = (int64_t)h[q].tiles_m * h[q].tiles_n;
         if ((int64_t)tiles + t >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
@@ -312,10 +315,207 @@ os_status create(const os_problem *problems, int32_t count, os_dtype a_t, os_dty
     return OS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The batched product with a caller-owned workspace and run-time masks
+// (oversketch_matmul_batched).  Each call: the GEMM descriptors are written into
+// the workspace by small kernels that carry them as launch parameters (so a
+// captured graph holds them by value), the sketches run on kBranches forked
+// streams (every block is sketched; CTAs of blocks that the device mask drops
+// return at once), then one grouped tcgen05 launch reads each product's mask
+// from device memory for its K list and its 1/k.  Nothing is allocated.
+
+constexpr int kBranches = 8;
+constexpr int kDescPerChunk = 40;
+
+struct DescChunk {
+    int32_t first, count;
+    GroupProblem items[kDescPerChunk];
+};
+static_assert(sizeof(DescChunk) <= 32000, "descriptor chunk exceeds the launch parameter space");
+
+__global__ void __launch_bounds__(256) upload_groups_kernel(const __grid_constant__ DescChunk chunk,
+                                                            GroupProblem *__restrict__ dst) {
+    const int words = chunk.count * (int)(sizeof(GroupProblem) / 16);
+    const uint4 *src = reinterpret_cast<const uint4 *>(chunk.items);
+    uint4 *out = reinterpret_cast<uint4 *>(dst + chunk.first);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) out[w] = src[w];
+}
+static_assert(sizeof(GroupProblem) % 16 == 0, "descriptors are copied in 16-byte words");
+
+struct BatchedLayout {
+    size_t desc, operands, slot, total;
+    std::vector<size_t> at_off, bt_off;
+};
+
+os_status batched_layout(int32_t count, const oversketch_plan_t *plans, const int64_t *m, const int64_t *n,
+                         const int64_t *l, os_dtype a_t, os_dtype b_t, BatchedLayout *L) {
+    if (count <= 0 || count > kMaxGroup || !plans || !m || !n || !l) return OS_ERR_INVALID_ARG;
+    if ((a_t != OS_F32 && a_t != OS_BF16) || (b_t != OS_F32 && b_t != OS_BF16)) return OS_ERR_DTYPE;
+    L->desc = align256(sizeof(GroupProblem) * (size_t)count);
+    L->at_off.assign(count, 0);
+    L->bt_off.assign(count, 0);
+    size_t off = 0, slot = 256;
+    for (int i = 0; i < count; ++i) {
+        const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
+        if (!p || m[i] < 0 || l[i] < 0 || n[i] != p->n) return OS_ERR_INVALID_ARG;
+        if (p->b % 64 != 0) return OS_ERR_UNSUPPORTED;   // BF16 GEMM K tile
+        const int64_t z = (int64_t)p->P * p->b;
+        L->at_off[i] = off;
+        off += align256((size_t)m[i] * z * 2);
+        L->bt_off[i] = off;
+        off += align256((size_t)l[i] * z * 2);
+        if (m[i] > 0 && l[i] > 0) {
+            slot = std::max(slot, sketch_workspace_bytes(p, m[i], a_t));
+            slot = std::max(slot, sketch_workspace_bytes(p, l[i], b_t));
+        }
+    }
+    L->operands = off;
+    L->slot = align256(slot);
+    const int W = std::min(kBranches, (int)count);
+    L->total = L->desc + L->operands + (size_t)W * L->slot + 256;
+    return OS_OK;
+}
+
+// Streams the sketches of a call fork onto, and the events of the fork and the
+// joins (one set per device, created on the first call; no event or stream is
+// created or destroyed while a stream may be capturing).  The lock serialises
+// the enqueueing of calls from several host threads on one device.
+struct Branches {
+    cudaStream_t stream[kBranches];
+    cudaEvent_t fork, join[kBranches];
+    std::mutex mu;
+};
+
+os_status branches_of(int dev, Branches **out) {
+    static Branches br[64];
+    static std::mutex mu;
+    if (dev < 0 || dev >= 64) return OS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(mu);
+    Branches &b = br[dev];
+    if (!b.fork) {
+        for (int w = 0; w < kBranches; ++w) {
+            OSK_CUDA_TRY(cudaStreamCreateWithFlags(&b.stream[w], cudaStreamNonBlocking));
+            OSK_CUDA_TRY(cudaEventCreateWithFlags(&b.join[w], cudaEventDisableTiming));
+        }
+        OSK_CUDA_TRY(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
+    }
+    *out = &b;
+    return OS_OK;
+}
+
 }  // namespace
 }  // namespace osk
 
 using namespace osk;
+
+extern "C" os_status oversketch_matmul_batched_workspace_size(int32_t count, const oversketch_plan_t *plans,
+                                                               const int64_t *m, const int64_t *n, const int64_t *l,
+                                                               os_dtype a_t, os_dtype b_t, const os_opts *opts,
+                                                               size_t *bytes) {
+    if (!bytes) return OS_ERR_INVALID_ARG;
+    if (opts && opts->gemm_dtype != OS_BF16) return OS_ERR_DTYPE;
+    BatchedLayout L;
+    OSK_TRY(batched_layout(count, plans, m, n, l, a_t, b_t, &L));
+    *bytes = L.total;
+    return OS_OK;
+}
+
+extern "C" os_status oversketch_matmul_batched(int32_t count, const oversketch_plan_t *plans,
+                                               const void *const *A, const void *const *B, float *const *C,
+                                               const int64_t *m, const int64_t *n, const int64_t *l, os_dtype a_t,
+                                               os_dtype b_t, const uint64_t *masks, const os_opts *opts,
+                                               void *workspace, size_t ws_bytes, void *stream) {
+    if (opts && (opts->gemm_dtype != OS_BF16 || opts->col_scale || opts->symmetric || opts->flags))
+        return opts->gemm_dtype != OS_BF16 ? OS_ERR_DTYPE : OS_ERR_UNSUPPORTED;
+    BatchedLayout L;
+    OSK_TRY(batched_layout(count, plans, m, n, l, a_t, b_t, &L));
+    if (!A || !B || !C || !masks) return OS_ERR_INVALID_ARG;
+    int dev = 0;
+    OSK_CUDA_TRY(cudaGetDevice(&dev));
+    std::vector<int> live;
+    for (int i = 0; i < count; ++i) {
+        const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
+        if (p->device != dev) return OS_ERR_INVALID_ARG;
+        if (m[i] == 0 || l[i] == 0) continue;   // an empty C_i: nothing to read or write
+        if (!A[i] || !B[i] || !C[i]) return OS_ERR_INVALID_ARG;
+        live.push_back(i);
+    }
+    if (live.empty()) return OS_OK;
+    if (!workspace || ws_bytes < L.total) return OS_ERR_WORKSPACE;
+    cudaStream_t st = as_stream(stream);
+    char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
+    GroupProblem *desc = reinterpret_cast<GroupProblem *>(base);
+    char *ops_base = base + L.desc;
+    char *slots = ops_base + L.operands;
+    // descriptors, longest K first (as for the batch object): the K of a product is
+    // only known on the device, so the order uses its whole sketch width
+    std::vector<int> ord = live;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+        const Plan *px = reinterpret_cast<const Plan *>(plans[x]), *py = reinterpret_cast<const Plan *>(plans[y]);
+        const int64_t kx = (int64_t)px->P * px->b, ky = (int64_t)py->P * py->b;
+        if (kx != ky) return kx > ky;
+        return m[x] * l[x] > m[y] * l[y];
+    });
+    const int cnt = (int)ord.size();
+    std::vector<GroupProblem> h(cnt);
+    int32_t tiles = 0;
+    for (int q = 0; q < cnt; ++q) {
+        const int i = ord[q];
+        const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
+        const int64_t z = (int64_t)p->P * p->b;
+        OSK_TRY(group_problem_bf16(&h[q], kGroupBN256, ops_base + L.at_off[i], z, ops_base + L.bt_off[i], z, m[i],
+                                   l[i], z, p->b, p->P, 0ull, masks + i, 1.f, 0.f, C[i], l[i]));
+        h[q].tile_begin = tiles;
+        const int64_t t = (int64_t)h[q].tiles_m * h[q].tiles_n;
+        if ((int64_t)tiles + t >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
+        tiles += (int32_t)t;
+    }
+    OSK_TRY(gemm_grouped_prepare());
+    for (int c0 = 0; c0 < cnt; c0 += kDescPerChunk) {
+        DescChunk chunk;
+        std::memset(&chunk, 0, sizeof(chunk));
+        chunk.first = c0;
+        chunk.count = std::min(kDescPerChunk, cnt - c0);
+        std::memcpy(chunk.items, h.data() + c0, sizeof(GroupProblem) * chunk.count);
+        upload_groups_kernel<<<1, 256, 0, st>>>(chunk, desc);
+        OSK_TRY(check_launch());
+    }
+    // sketches on forked streams, heaviest first, greedy by work
+    Branches *br = nullptr;
+    OSK_TRY(branches_of(dev, &br));
+    const int W = std::min(kBranches, cnt);
+    std::vector<int> sk = live;
+    auto work = [&](int i) { return (m[i] + l[i]) * n[i]; };
+    std::stable_sort(sk.begin(), sk.end(), [&](int x, int y) { return work(x) > work(y); });
+    std::vector<int64_t> load(W, 0);
+    std::vector<std::vector<int>> branch(W);
+    for (int i : sk) {
+        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        branch[w].push_back(i);
+        load[w] += work(i);
+    }
+    {
+        std::lock_guard<std::mutex> lock(br->mu);
+        OSK_CUDA_TRY(cudaEventRecord(br->fork, st));
+        for (int w = 0; w < W; ++w) {
+            cudaStream_t bs = br->stream[w];
+            OSK_CUDA_TRY(cudaStreamWaitEvent(bs, br->fork, 0));
+            void *ws = slots + (size_t)w * L.slot;
+            for (int i : branch[w]) {
+                const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
+                const int64_t z = (int64_t)p->P * p->b;
+                const uint64_t all = p->P >= 64 ? ~0ull : ((1ull << p->P) - 1ull);
+                OSK_TRY(sketch_left_impl(p, A[i], a_t, m[i], n[i], ops_base + L.at_off[i], OS_BF16, z, nullptr, nullptr,
+                                         all, ws, L.slot, bs, masks + i));
+                OSK_TRY(sketch_right_impl(p, B[i], b_t, l[i], l[i], ops_base + L.bt_off[i], OS_BF16, z, nullptr, all, ws,
+                                          L.slot, bs, nullptr, masks + i));
+            }
+            OSK_CUDA_TRY(cudaEventRecord(br->join[w], bs));
+            OSK_CUDA_TRY(cudaStreamWaitEvent(st, br->join[w], 0));
+        }
+    }
+    return gemm_grouped_bf16(desc, cnt, tiles, kGroupBN256, st);
+}
 
 extern "C" os_status oversketch_batch_create(const os_problem *problems, int32_t count, os_dtype a_t,
                                              os_dtype b_t, os_dtype gemm_dtype, size_t workspace_limit,

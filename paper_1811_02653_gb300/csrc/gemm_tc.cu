@@ -149,7 +149,7 @@ __device__ __forceinline__ int find_problem(const int32_t *begin, int count, int
 // Everything one role needs to know about a tile.
 struct TileJob {
     const CUtensorMap *ta, *tb;
-    const int32_t *kept;          // kept block indices
+    uint64_t mask;                // grouped launches: kept sketch blocks (bit j = block j)
     int tm, tn;
     int num_kb, kb_per_blk, b;
     float *C;
@@ -236,21 +236,23 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             tile_coords(t - s_begin[p], P->tiles_m, P->tiles_n, j.tm, j.tn);
             j.ta = &P->ta;
             j.tb = &P->tb;
-            j.kept = P->kept.idx;
-            j.num_kb = P->num_kb;
+            j.mask = group_mask(P);
+            const int k = __popcll(j.mask);
+            j.num_kb = k * P->kb_per_blk;
             j.kb_per_blk = P->kb_per_blk;
             j.b = P->b;
             j.C = P->C;
             j.m = P->m;
             j.l = P->l;
             j.ldc = P->ldc;
-            j.alpha = P->alpha;
+            // a run-time mask brings its own 1/k; an empty one gives a zero product
+            j.alpha = P->dmask ? (k ? P->alpha / (float)k : 0.f) : P->alpha;
             j.beta = P->beta;
         } else {
             tile_coords(t, g.tiles_m, g.tiles_n, j.tm, j.tn);
             j.ta = &tmap_a0;
             j.tb = &tmap_b0;
-            j.kept = nullptr;             // read g.kept directly (no copy of the parameter)
+            j.mask = 0;                   // read g.kept directly (no copy of the parameter)
             j.num_kb = g.num_kb;
             j.kb_per_blk = g.kb_per_blk;
             j.b = g.b;
@@ -264,8 +266,12 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
         return j;
     };
     auto num_kb_of = [&](int t) -> int {
-        if constexpr (GROUPED) return g.group[find_problem(s_begin, g.group_count, t)].num_kb;
-        else return g.num_kb;
+        if constexpr (GROUPED) {
+            const GroupProblem *P = g.group + find_problem(s_begin, g.group_count, t);
+            return __popcll(group_mask(P)) * P->kb_per_blk;
+        } else {
+            return g.num_kb;
+        }
     };
 
     if (warp == 0) {
@@ -279,17 +285,32 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
             bool ok = true;
             for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
                 const TileJob j = job(t);
+                uint64_t rest = j.mask;          // grouped: kept blocks not yet started
+                int kidx = 0;
+                if constexpr (GROUPED) {
+                    // the descriptors' tensor maps may have been written by a kernel
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(j.ta) : "memory");
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(j.tb) : "memory");
+                }
                 for (int kb = 0; kb < j.num_kb; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, abort, wait_ns)) { ok = false; break; }
+                    const int blk = kb / j.kb_per_blk;
+                    const int kin = kb - blk * j.kb_per_blk;
+                    if constexpr (GROUPED) {
+                        if (kin == 0) {
+                            kidx = __ffsll((long long)rest) - 1;
+                            rest &= rest - 1;
+                        }
+                    } else {
+                        kidx = g.kept.idx[blk];
+                    }
                     if (t == blockIdx.x && kb == skip_kb) {
                         // test hook: this stage is never loaded nor armed, so the
                         // MMA warp's wait for it runs out
                         if (++stage == STAGES) stage = 0, phase ^= 1u;
                         continue;
                     }
-                    const int blk = kb / j.kb_per_blk;
-                    const int kidx = GROUPED ? j.kept[blk] : g.kept.idx[blk];
-                    const int kz = kidx * j.b + (kb - blk * j.kb_per_blk) * BKE;
+                    const int kz = kidx * j.b + kin * BKE;
                     uint8_t *st = tiles + stage * C::STAGE_BYTES;
                     mbar_expect_tx(&full[stage], C::TX_BYTES);
                     tma_load_2d(j.ta, &full[stage], st, kz, j.tm * BM);
@@ -320,6 +341,18 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
         bool any = false;
         for (int t = blockIdx.x; ok && t < g.num_tiles; t += gridDim.x) {
           const int num_kb = num_kb_of(t);
+          if (GROUPED && num_kb == 0) {
+              // a product whose run-time mask keeps no block: hand the epilogue an
+              // accumulator (no MMA issued; it writes zeros)
+              const int a = iter & 1;
+              const uint32_t aphase = (uint32_t)(iter >> 1) & 1u;
+              ++iter;
+              if (!__all_sync(0xffffffffu, mbar_wait(&tmem_empty[a], aphase ^ 1u, abort, wait_ns))) { ok = false; break; }
+              tc_fence_after();
+              if (lane == 0) umma_commit(&tmem_full[a]);
+              __syncwarp();
+              continue;
+          }
           for (int kc = 0; ok && kc < num_kb; kc += C::CHUNK_KB, ++iter) {
             const int kc_end = min(num_kb, kc + C::CHUNK_KB);
             const int a = iter & 1;
@@ -489,8 +522,13 @@ gemm_masked_tc_kernel(const __grid_constant__ CUtensorMap tmap_a0, const __grid_
                 tc_fence_after();
                 for (int ch = 0; ch < BN / 32; ++ch) {
                     uint32_t v[32];
-                    tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
-                                           (uint32_t)(a * C::ACC_STRIDE + ch * 32), v);
+                    if (j.num_kb > 0) {
+                        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                               (uint32_t)(a * C::ACC_STRIDE + ch * 32), v);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) v[u] = 0u;   // no kept block: a zero product
+                    }
                     store32(j, vec_ok, r, c0 + ch * 32, reinterpret_cast<const float *>(v));
                 }
                 tc_fence_before();
@@ -955,11 +993,11 @@ os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const floa
 }
 
 os_status group_problem_bf16(GroupProblem *gp, GroupTile tile, const void *A, int64_t lda, const void *B,
-                             int64_t ldb, int64_t m, int64_t l, int64_t zK, int32_t blk, const BlockList &kept,
-                             float alpha, float beta, float *C, int64_t ldc) {
+                             int64_t ldb, int64_t m, int64_t l, int64_t zK, int32_t blk, int32_t P, uint64_t mask,
+                             const uint64_t *dmask, float alpha, float beta, float *C, int64_t ldc) {
     const int BN = tile == kGroupBN256 ? CfgBf16::BN : CfgBf16N128::BN;
     constexpr int BKE = CfgBf16::BKE;
-    if (m <= 0 || l <= 0 || kept.count <= 0) return OS_ERR_INVALID_ARG;
+    if (m <= 0 || l <= 0 || P < 1 || P > 64 || (!dmask && mask == 0)) return OS_ERR_INVALID_ARG;
     if (blk % BKE != 0) return OS_ERR_UNSUPPORTED;
     if (!aligned16(A) || !aligned16(B) || (lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0) return OS_ERR_INVALID_ARG;
     if (zK >= (int64_t(1) << 31)) return OS_ERR_UNSUPPORTED;
@@ -974,11 +1012,12 @@ os_status group_problem_bf16(GroupProblem *gp, GroupTile tile, const void *A, in
     gp->beta = beta;
     gp->b = blk;
     gp->kb_per_blk = blk / BKE;
-    gp->num_kb = kept.count * gp->kb_per_blk;
+    gp->P = P;
     gp->tiles_m = (int32_t)((m + BM - 1) / BM);
     gp->tiles_n = (int32_t)((l + BN - 1) / BN);
     gp->tile_begin = 0;
-    gp->kept = kept;
+    gp->mask = mask;
+    gp->dmask = dmask;
     return OS_OK;
 }
 
@@ -1007,8 +1046,14 @@ os_status launch_grouped(const GroupProblem *probs, int32_t count, int32_t total
 }  // namespace
 
 os_status gemm_grouped_prepare() {
+    static std::mutex mu;
+    static bool done = false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done) return OS_OK;
     OSK_TRY(prepare_grouped<CfgBf16>());
-    return prepare_grouped<CfgBf16N128>();
+    OSK_TRY(prepare_grouped<CfgBf16N128>());
+    done = true;
+    return OS_OK;
 }
 
 os_status gemm_grouped_bf16(const GroupProblem *probs, int32_t count, int32_t total_tiles, GroupTile tile,

@@ -19,7 +19,7 @@ namespace osk {
 os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
                            const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
-                           cudaStream_t st);
+                           cudaStream_t st, const uint64_t *dmask = nullptr);
 size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t);
 os_status sketch_left_check(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda, void *At,
                             os_dtype out_t, int64_t ldat, float *scales, uint64_t block_mask);

@@ -122,7 +122,8 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                      const uint32_t *__restrict__ pperm, const uint32_t *__restrict__ poffs,
                      int64_t pstride, int32_t b, int32_t z, const float *__restrict__ wts,
                      OutT *__restrict__ Yt, int64_t ldy, float *__restrict__ scales,
-                     int64_t lds, BlockList blocks, int32_t tiles_per_block, int64_t plane_elems) {
+                     int64_t lds, BlockList blocks, int32_t tiles_per_block, int64_t plane_elems,
+                     const uint64_t *__restrict__ dmask) {
     constexpr int SUBS = 32 / SLOTS;     // lanes per member
     constexpr int VW = 16 / (int)sizeof(InT);   // free indices per lane: 16 bytes
     constexpr int TF = VW * SUBS;        // free indices per CTA (one strip)
@@ -141,6 +142,8 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
     const int q0 = jblk * b + (blockIdx.x - bt * tiles_per_block) * QT;
     const int qend = min(z, jblk * b + b);
     const int64_t f0 = (int64_t)blockIdx.y * TF;
+    // a block mask read at run time: CTAs of blocks it does not keep have nothing to do
+    if (dmask && !((__ldg(dmask) >> jblk) & 1ull)) return;
     using L = Loader<InT, VW, true>;
 
     const int nb = min(QPW, qend - q0 - warp * QPW);   // buckets owned by this warp
@@ -565,7 +568,8 @@ os_status launch_entry_weights(const Plan *p, const float *s, uint64_t block_mas
 template <typename InT, typename OutT, int QT, int SLOTS>
 os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int64_t ldx, int64_t F,
                           const float *wts, void *Yt, int64_t ldy, float *scales, int64_t scale_ld,
-                          const BlockList &blocks, cudaStream_t st, int64_t plane_elems = 0) {
+                          const BlockList &blocks, cudaStream_t st, int64_t plane_elems = 0,
+                          const uint64_t *dmask = nullptr) {
     const int z = p->P * p->b;
     const int tpb = (p->b + QT - 1) / QT;
     constexpr int TF = strip_of<InT>() / SLOTS;
@@ -592,10 +596,10 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
         cfg.numAttrs = 1;
         OSK_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, X, strip_stride, ldx, F, (const uint32_t *)p->pperm,
                                         (const uint32_t *)p->poffs, p->pstride, p->b, z, wts, (OutT *)Yt, ldy,
-                                        scales, scale_ld, blocks, tpb, plane_elems));
+                                        scales, scale_ld, blocks, tpb, plane_elems, dmask));
     } else {
         k<<<grid, kWarps * 32, smem, st>>>(X, strip_stride, ldx, F, p->pperm, p->poffs, p->pstride, p->b, z,
-                                          wts, (OutT *)Yt, ldy, scales, scale_ld, blocks, tpb, plane_elems);
+                                          wts, (OutT *)Yt, ldy, scales, scale_ld, blocks, tpb, plane_elems, dmask);
     }
     return check_launch();
 }
@@ -611,22 +615,22 @@ constexpr int kGatherQT = 16;
 template <typename InT>
 os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *wts, void *Yt,
                         os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask,
-                        cudaStream_t st, int64_t plane_rows = 0) {
+                        cudaStream_t st, int64_t plane_rows = 0, const uint64_t *dmask = nullptr) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
     constexpr int64_t W = strip_of<InT>();
     const int64_t ss = p->n * W;
     switch (out_t) {
         case OS_F32:
-            return launch_gather_t<InT, float, kGatherQT, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld, blocks, st);
+            return launch_gather_t<InT, float, kGatherQT, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld, blocks, st, 0, dmask);
         case OS_BF16:
             return launch_gather_t<InT, __nv_bfloat16, kGatherQT, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld,
-                                                              blocks, st);
+                                                              blocks, st, 0, dmask);
         case OS_FP8E4M3:
             return launch_gather_t<InT, __nv_fp8_e4m3, 32, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld,
-                                                               blocks, st);
+                                                               blocks, st, 0, dmask);
         case OS_TF32X2:
             return launch_gather_t<InT, Tf32Pair, kGatherQT, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld, blocks,
-                                                         st, plane_rows * ldy);
+                                                         st, plane_rows * ldy, dmask);
     }
     return OS_ERR_DTYPE;
 }
@@ -636,20 +640,21 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *wt
 // packing pass is needed).  F must be a multiple of 128.
 os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, const float *wts,
                                void *Yt, os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld,
-                               uint64_t block_mask, cudaStream_t st, int64_t plane_rows = 0) {
+                               uint64_t block_mask, cudaStream_t st, int64_t plane_rows = 0,
+                               const uint64_t *dmask = nullptr) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
         switch (out_t) {
         case OS_F32:
-            return launch_gather_t<float, float, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld, blocks, st);
+            return launch_gather_t<float, float, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld, blocks, st, 0, dmask);
         case OS_BF16:
             return launch_gather_t<float, __nv_bfloat16, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld,
-                                                                blocks, st);
+                                                                blocks, st, 0, dmask);
         case OS_FP8E4M3:
             return launch_gather_t<float, __nv_fp8_e4m3, 32, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, scales, scale_ld,
-                                                                 blocks, st);
+                                                                 blocks, st, 0, dmask);
         case OS_TF32X2:
             return launch_gather_t<float, Tf32Pair, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld, blocks,
-                                                           st, plane_rows * ldy);
+                                                           st, plane_rows * ldy, dmask);
     }
     return OS_ERR_DTYPE;
 }
@@ -747,7 +752,7 @@ os_status sketch_left_check(const Plan *p, const void *A, os_dtype a_t, int64_t 
 os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
                            const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
-                           cudaStream_t st) {
+                           cudaStream_t st, const uint64_t *dmask = nullptr) {
     OSK_TRY(sketch_left_check(p, A, a_t, m, lda, At, out_t, ldat, scales, block_mask));
     if (m == 0) return OS_OK;
     if (!ws || ws_bytes < sketch_workspace_bytes(p, m, a_t)) return OS_ERR_WORKSPACE;
@@ -757,16 +762,17 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
     if (a_t == OS_F32) {
         OSK_TRY(launch_pack_cols<float>((const float *)A, lda, m, p->n, (float *)Xs, st));
         return launch_gather<float>(p, (const float *)Xs, m, wts, At, out_t, ldat, scales, fp8_scale_ld(m),
-                                    block_mask, st, m);
+                                    block_mask, st, m, dmask);
     }
     OSK_TRY(launch_pack_cols<__nv_bfloat16>((const __nv_bfloat16 *)A, lda, m, p->n, (__nv_bfloat16 *)Xs, st));
     return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, m, wts, At, out_t, ldat, scales,
-                                        fp8_scale_ld(m), block_mask, st, m);
+                                        fp8_scale_ld(m), block_mask, st, m, dmask);
 }
 
 os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t l, int64_t ldb,
                             void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
-                            void *ws, size_t ws_bytes, cudaStream_t st, const float *row_scale) {
+                            void *ws, size_t ws_bytes, cudaStream_t st, const float *row_scale = nullptr,
+                            const uint64_t *dmask = nullptr) {
     if (!p || l < 0) return OS_ERR_INVALID_ARG;
     if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (b_t != OS_F32 && b_t != OS_BF16) return OS_ERR_DTYPE;
@@ -786,13 +792,13 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
         const float *wts = nullptr;
         if (row_scale) OSK_TRY(make_weights(p, row_scale, block_mask, ws_weights(p, ws, l - lf, b_t), &wts, st));
         OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, wts, BtT, out_t, ldbt, scales,
-                                     fp8_scale_ld(l), block_mask, st, l));
+                                     fp8_scale_ld(l), block_mask, st, l, dmask));
         if (lf == l) return OS_OK;
         float *Xs = (float *)ws_base(ws);
         OSK_TRY(launch_pack_rows<float>((const float *)B + lf, ldb, p->n, l - lf, Xs, st));
         char *yt = (char *)BtT + (size_t)lf * ldbt * dtype_size(out_t);
         float *sc = scales ? scales + lf : nullptr;   // slice-major: the remainder's rows start at lf
-        return launch_gather<float>(p, Xs, l - lf, wts, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask, st, l);
+        return launch_gather<float>(p, Xs, l - lf, wts, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask, st, l, dmask);
     }
     if (!ws || ws_bytes < sketch_workspace_bytes(p, l, b_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);
@@ -801,11 +807,11 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
     if (b_t == OS_F32) {
         OSK_TRY(launch_pack_rows<float>((const float *)B, ldb, p->n, l, (float *)Xs, st));
         return launch_gather<float>(p, (const float *)Xs, l, wts, BtT, out_t, ldbt, scales, fp8_scale_ld(l),
-                                    block_mask, st, l);
+                                    block_mask, st, l, dmask);
     }
     OSK_TRY(launch_pack_rows<__nv_bfloat16>((const __nv_bfloat16 *)B, ldb, p->n, l, (__nv_bfloat16 *)Xs, st));
     return launch_gather<__nv_bfloat16>(p, (const __nv_bfloat16 *)Xs, l, wts, BtT, out_t, ldbt, scales,
-                                        fp8_scale_ld(l), block_mask, st, l);
+                                        fp8_scale_ld(l), block_mask, st, l, dmask);
 }
 
 os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t ldt, uint64_t mask,

@@ -109,6 +109,10 @@ def load_library(path: str | None = None):
             "oversketch_batch_info": (st, [vp, ctypes.POINTER(_BatchInfo)]),
             "oversketch_batch_destroy": (st, [vp]),
             "oversketch_test_wait_timeout": (st, [u64, i32]),
+            "oversketch_matmul_batched_workspace_size": (st, [i32, vp, vp, vp, vp, st, st, ctypes.POINTER(_Opts),
+                                                              ctypes.POINTER(sz)]),
+            "oversketch_matmul_batched": (st, [i32, vp, vp, vp, vp, vp, vp, vp, st, st, vp, ctypes.POINTER(_Opts), vp,
+                                               sz, vp]),
             "oversketch_matmul_backward_workspace_size": (st, [vp, i64, i64, u64, i32, i32, ctypes.POINTER(sz)]),
             "oversketch_matmul_backward": (st, [vp, vp, i64, vp, i64, vp, i64, i64, i64, u64, vp, st, i64, vp, st,
                                                 i64, vp, sz, vp]),
@@ -137,6 +141,7 @@ def _sigs_names():
             "oversketch_batch_destroy", "oversketch_sketch_left_sparse",
             "oversketch_matmul_host_workspace_size", "oversketch_matmul_host", "oversketch_sketch_size",
             "oversketch_gemm_masked_blocks", "oversketch_matmul_backward_workspace_size", "oversketch_test_wait_timeout",
+            "oversketch_matmul_batched_workspace_size", "oversketch_matmul_batched",
             "oversketch_matmul_backward"]
 
 
@@ -585,6 +590,54 @@ def cast(X, out_dtype, out=None, stream=None):
     _check(load_library().oversketch_cast(_ptr(X), _dt(X), rows, cols, ldx, _ptr(out), od, out.stride(0),
                                           _stream(stream)), "oversketch_cast")
     return out
+
+
+def _batched_arrays(plans, ms, ns, ls):
+    cnt = len(plans)
+    P = (ctypes.c_void_p * cnt)(*[p.handle.value for p in plans])
+    M = (ctypes.c_int64 * cnt)(*ms)
+    Nn = (ctypes.c_int64 * cnt)(*ns)
+    Lr = (ctypes.c_int64 * cnt)(*ls)
+    return P, M, Nn, Lr
+
+
+def matmul_batched_workspace(plans, ms, ns, ls, a_dtype=torch.float32, b_dtype=torch.float32) -> int:
+    P, M, Nn, Lr = _batched_arrays(plans, ms, ns, ls)
+    out = ctypes.c_size_t()
+    o = _opts("bf16")
+    _check(load_library().oversketch_matmul_batched_workspace_size(
+        len(plans), P, M, Nn, Lr, _dtype_code(a_dtype), _dtype_code(b_dtype), ctypes.byref(o), ctypes.byref(out)),
+        "oversketch_matmul_batched_workspace_size")
+    return out.value
+
+
+def matmul_batched(plans, As, Bs, Cs, masks, workspace=None, stream=None):
+    """C_p = (1/k_p)(A_p S_p)(S_p^T B_p) for every p in one call (BF16 GEMM),
+    the kept blocks of product p read from masks[p] on the device when the work
+    runs (masks: int64 CUDA tensor of len(plans) words).  A_p, B_p: row-major
+    CUDA tensors (one dtype per side), C_p: FP32 m_p x l_p, all contiguous."""
+    cnt = len(plans)
+    ms = [A.shape[0] for A in As]
+    ns = [A.shape[1] for A in As]
+    ls = [B.shape[1] for B in Bs]
+    a_t, b_t = _dt(As[0]), _dt(Bs[0])
+    for A, B, C in zip(As, Bs, Cs):
+        if not (A.is_contiguous() and B.is_contiguous() and C.is_contiguous()):
+            raise OverSketchError("matmul_batched: A, B and C must be contiguous")
+        if _dt(A) != a_t or _dt(B) != b_t or C.dtype != torch.float32:
+            raise OverSketchError("matmul_batched: one dtype per operand side, FP32 C")
+    P, M, Nn, Lr = _batched_arrays(plans, ms, ns, ls)
+    Ap = (ctypes.c_void_p * cnt)(*[A.data_ptr() for A in As])
+    Bp = (ctypes.c_void_p * cnt)(*[B.data_ptr() for B in Bs])
+    Cp = (ctypes.c_void_p * cnt)(*[C.data_ptr() for C in Cs])
+    if workspace is None:
+        workspace = torch.empty(matmul_batched_workspace(plans, ms, ns, ls, As[0].dtype, Bs[0].dtype),
+                                dtype=torch.uint8, device=As[0].device)
+    o = _opts("bf16")
+    _check(load_library().oversketch_matmul_batched(
+        cnt, P, Ap, Bp, Cp, M, Nn, Lr, a_t, b_t, _ptr(masks), ctypes.byref(o), _ptr(workspace), workspace.numel(),
+        _stream(stream)), "oversketch_matmul_batched")
+    return Cs
 
 
 class Batch:

@@ -133,3 +133,46 @@ def test_batched_argument_errors(ops):
         ops.Batch([(A, B, C, ops.plan(A.shape[1] + 64, 64, 4, 1, 0), mask)])     # plan dimension != n
     with pytest.raises(ops.OverSketchError, match="OS_ERR_MASK"):
         ops.Batch([(A, B, C, plan, 1 << 7)])                                     # block past N + e
+
+
+def test_matmul_batched_device_masks_in_one_captured_graph(ops):
+    # oversketch_matmul_batched reads every product's kept blocks from device
+    # memory when the work runs: ONE captured graph, replayed with three different
+    # straggler sets (including an empty mask: a zero product), matches the oracle
+    # every time.  The call allocates nothing (caller workspace), so it can be
+    # recorded inside torch's graph capture.
+    rng = np.random.default_rng(41)
+    probs = _problems(rng, 9)
+    probs[3]["m"], probs[3]["A"] = 0, probs[3]["A"][:0]        # an empty product is skipped
+    dev = _device(ops, probs)
+    plans = [d[3] for d in dev]
+    As, Bs, Cs = [d[0] for d in dev], [d[1] for d in dev], [d[2] for d in dev]
+    P = probs[0]["N"] + probs[0]["e"]
+    masks = torch.zeros(len(probs), dtype=torch.int64, device="cuda")
+    ws = torch.empty(ops.matmul_batched_workspace(plans, [A.shape[0] for A in As], [A.shape[1] for A in As],
+                                                  [B.shape[1] for B in Bs]), dtype=torch.uint8, device="cuda")
+    masks.copy_(torch.tensor([q["mask"] for q in probs], dtype=torch.int64))
+    ops.matmul_batched(plans, As, Bs, Cs, masks, workspace=ws)      # first call: library streams, attributes
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ops.matmul_batched(plans, As, Bs, Cs, masks, workspace=ws)
+    sets = [[q["mask"] for q in probs],
+            [((1 << P) - 1) & ~(0b11 << (p % (P - 1))) for p in range(len(probs))],   # two stragglers each
+            [0 if p == 5 else (1 << (p % P)) for p in range(len(probs))]]              # one block / none
+    for msk in sets:
+        masks.copy_(torch.tensor(msk, dtype=torch.int64))
+        for C in Cs:
+            C.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for p, (q, C) in enumerate(zip(probs, Cs)):
+            if q["m"] == 0:
+                continue
+            ref = _bf16_oracle(dict(q, mask=msk[p])) if msk[p] else np.zeros((q["m"], q["l"]))
+            got = C.cpu().numpy()
+            if msk[p]:
+                assert oracle.rel_frob(got, ref) <= 1e-4, (p, msk[p])
+            else:
+                assert np.array_equal(got, ref)
+    assert ops.device_status() == 0
