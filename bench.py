@@ -214,6 +214,32 @@ def run_reference(args):
     return 0
 
 
+def _time_plans(ops, w, runs: int):
+    """Host wall times of oversketch_plan (table allocation, hash, bucket-CSR,
+    synchronise) and the device time between CUDA events on its stream."""
+    import torch
+    host, dev = [], []
+    st = torch.cuda.current_stream()
+    for _ in range(runs):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(st)
+        q = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
+        e1.record(st)
+        host.append(time.perf_counter() - t0)
+        e1.synchronize()
+        dev.append(e0.elapsed_time(e1))
+        q.destroy()
+    return host, dev
+
+
+def _plan_record(host_s, dev_ms):
+    return {"median": statistics.median(host_s) * 1e3, "device_median": statistics.median(dev_ms), "runs": len(host_s),
+            "what": "oversketch_plan: host wall time (table allocation, hash, bucket-CSR, synchronise) and the "
+                    "device time between CUDA events around it"}
+
+
 def _sketch_dtype(gemm_dtype: str, b: int) -> str:
     """Sketch output dtype of a GEMM dtype: the FP32 product runs as 3xTF32 on the
     tensor cores, so its sketches emit hi/lo planes."""
@@ -276,11 +302,7 @@ def run_ours(args):
     del Bt_h
     # plan creation (hash tables + bucket-CSR; oversketch_plan synchronises), timed
     # on its own: the same S serves every product, so it is outside the step
-    plan_s = []
-    for _ in range(3):
-        t0 = time.perf_counter()
-        ops.plan(w.n, w.b, w.N, w.e, w.hash_seed).destroy()
-        plan_s.append(time.perf_counter() - t0)
+    plan_s, plan_dev = _time_plans(ops, w, 3)
     p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
     gd = args.dtype
     sd = _sketch_dtype(gd, w.b)
@@ -505,8 +527,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": 4 * args.steps, "clocks": clk, "error": err, "exact_gemm": exact,
             "forms": forms,
-            "plan_ms": {"median": statistics.median(plan_s) * 1e3, "runs": len(plan_s),
-                        "what": "oversketch_plan host wall time: table allocation, hash, bucket-CSR, synchronise"}}
+            "plan_ms": _plan_record(plan_s, plan_dev)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -605,11 +626,7 @@ def run_small(args):
     A_h = torch.from_numpy(w.left()).pin_memory()
     B_h = torch.from_numpy(w.right()).pin_memory()
     A, B = A_h.to(dev), B_h.to(dev)
-    plan_s = []
-    for _ in range(5):
-        t0 = time.perf_counter()
-        ops.plan(w.n, w.b, w.N, w.e, w.hash_seed).destroy()
-        plan_s.append(time.perf_counter() - t0)
+    plan_s, plan_dev = _time_plans(ops, w, 5)
     p = ops.plan(w.n, w.b, w.N, w.e, w.hash_seed)
     gd = args.dtype
     sd = _sketch_dtype(gd, w.b)
@@ -711,8 +728,7 @@ def run_small(args):
                  3 * args.steps, clk, err, world,
                  warm_l2={"ms_per_step": warm_ms, "tflops": _job_value(flop, warm_ms, world),
                           "phases_ms": {k_: round(v_, 4) for k_, v_ in warm_per.items()}},
-                 plan_ms={"median": statistics.median(plan_s) * 1e3, "runs": len(plan_s),
-                          "what": "oversketch_plan host wall time: table allocation, hash, bucket-CSR, synchronise"})
+                 plan_ms=_plan_record(plan_s, plan_dev))
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

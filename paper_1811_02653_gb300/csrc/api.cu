@@ -170,6 +170,7 @@ extern "C" os_status oversketch_gemm_masked(oversketch_plan_t plan, const void *
                                             const float *b_scales, os_dtype dt, int64_t m, int64_t l,
                                             uint64_t mask, float alpha, float beta, float *C,
                                             int64_t ldc, void *stream) {
+    OSK_NVTX("gemm_masked");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     if (!p || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_mask(mask, p->P));
@@ -208,6 +209,7 @@ extern "C" os_status oversketch_matmul(oversketch_plan_t plan, const void *A, os
                                        float *C, int64_t ldc, int64_t m, int64_t n, int64_t l,
                                        uint64_t mask, const os_opts *opts, void *workspace,
                                        size_t ws_bytes, void *stream) {
+    OSK_NVTX("matmul");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     if (!p) return OS_ERR_INVALID_ARG;
     const bool sym = opts && opts->symmetric;
@@ -341,6 +343,7 @@ extern "C" os_status oversketch_matmul_host(oversketch_plan_t plan, const void *
                                             const void *B, os_dtype b_t, int64_t ldb, float *C, int64_t ldc,
                                             int64_t m, int64_t n, int64_t l, uint64_t mask, const os_opts *opts,
                                             void *workspace, size_t ws_bytes, void *stream) {
+    OSK_NVTX("matmul_host");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     if (!p) return OS_ERR_INVALID_ARG;
     const bool sym = opts && opts->symmetric;
@@ -509,6 +512,7 @@ extern "C" os_status oversketch_matmul_backward(oversketch_plan_t plan, const vo
                                                 int64_t m, int64_t l, uint64_t mask, void *dX, os_dtype x_t,
                                                 int64_t ldx, void *dG, os_dtype g_t, int64_t ldg, void *workspace,
                                                 size_t ws_bytes, void *stream) {
+    OSK_NVTX("matmul_backward");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     if (!p || m < 0 || l < 0 || lddc < l) return OS_ERR_INVALID_ARG;
     OSK_TRY(check_mask(mask, p->P));

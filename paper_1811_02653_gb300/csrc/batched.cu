@@ -425,6 +425,7 @@ extern "C" os_status oversketch_matmul_batched(int32_t count, const oversketch_p
                                                const int64_t *m, const int64_t *n, const int64_t *l, os_dtype a_t,
                                                os_dtype b_t, const uint64_t *masks, const os_opts *opts,
                                                void *workspace, size_t ws_bytes, void *stream) {
+    OSK_NVTX("matmul_batched");
     if (opts && (opts->gemm_dtype != OS_BF16 || opts->col_scale || opts->symmetric || opts->flags))
         return opts->gemm_dtype != OS_BF16 ? OS_ERR_DTYPE : OS_ERR_UNSUPPORTED;
     BatchedLayout L;
@@ -535,6 +536,7 @@ extern "C" os_status oversketch_batch_create(const os_problem *problems, int32_t
 }
 
 extern "C" os_status oversketch_batch_run(oversketch_batch_t batch, void *stream) {
+    OSK_NVTX("batch_run");
     Batch *B = reinterpret_cast<Batch *>(batch);
     if (!B || !B->exec) return OS_ERR_INVALID_ARG;
     int dev = 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -49,6 +50,16 @@ BlockList mask_to_list(uint64_t mask, int P);
 os_status check_mask(uint64_t mask, int P);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// NVTX range over a host call (plan, sketches, GEMM, product): shows the path's
+// phases on a profiler timeline; a no-op when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define OSK_NVTX(name) ::osk::NvtxRange osk_nvtx_range_(name)
 
 inline size_t dtype_size(os_dtype t) {   // bytes per element of one plane
     return (t == OS_F32 || t == OS_TF32X2) ? 4 : (t == OS_BF16 ? 2 : 1);

@@ -1094,6 +1094,7 @@ extern "C" os_status oversketch_test_wait_timeout(uint64_t limit_ns, int32_t ski
 extern "C" os_status oversketch_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m,
                                           int64_t n, int64_t K, float alpha, float beta, float *C, int64_t ldc,
                                           void *stream) {
+    OSK_NVTX("gemm_bf16");
     if (m < 0 || n < 0 || K < 0 || ldc < n || lda < K || ldb < K) return OS_ERR_INVALID_ARG;
     if (m == 0 || n == 0) return OS_OK;   // an empty C
     if (!A || !B || !C) return OS_ERR_INVALID_ARG;
@@ -1110,6 +1111,7 @@ extern "C" os_status oversketch_gemm_masked_blocks(oversketch_plan_t plan, const
                                                    const void *BtT, int64_t ldbt, int64_t m, int64_t l,
                                                    const uint64_t *block_masks, int64_t bm, int64_t bn,
                                                    float beta, float *C, int64_t ldc, void *stream) {
+    OSK_NVTX("gemm_masked_blocks");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     if (!p || m < 0 || l < 0 || ldc < l) return OS_ERR_INVALID_ARG;
     if (bm < 256 || bn < 256 || bm % 256 != 0 || bn % 256 != 0) return OS_ERR_UNSUPPORTED;

@@ -753,6 +753,7 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
                            const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
                            cudaStream_t st, const uint64_t *dmask = nullptr) {
+    OSK_NVTX("sketch_left");
     OSK_TRY(sketch_left_check(p, A, a_t, m, lda, At, out_t, ldat, scales, block_mask));
     if (m == 0) return OS_OK;
     if (!ws || ws_bytes < sketch_workspace_bytes(p, m, a_t)) return OS_ERR_WORKSPACE;
@@ -773,6 +774,7 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
                             void *BtT, os_dtype out_t, int64_t ldbt, float *scales, uint64_t block_mask,
                             void *ws, size_t ws_bytes, cudaStream_t st, const float *row_scale = nullptr,
                             const uint64_t *dmask = nullptr) {
+    OSK_NVTX("sketch_right");
     if (!p || l < 0) return OS_ERR_INVALID_ARG;
     if (block_mask) OSK_TRY(check_mask(block_mask, p->P));
     if (b_t != OS_F32 && b_t != OS_BF16) return OS_ERR_DTYPE;
@@ -915,6 +917,7 @@ extern "C" os_status oversketch_sketch_right(oversketch_plan_t plan, const void 
 extern "C" os_status oversketch_unsketch_cols(oversketch_plan_t plan, const float *T, int64_t m,
                                               int64_t ldt, uint64_t mask, float scale, void *dX,
                                               os_dtype x_t, int64_t ldx, void *stream) {
+    OSK_NVTX("unsketch_cols");
     return unsketch_cols_impl(reinterpret_cast<const Plan *>(plan), T, m, ldt, mask, scale, dX, x_t,
                               ldx, as_stream(stream));
 }
@@ -922,6 +925,7 @@ extern "C" os_status oversketch_unsketch_cols(oversketch_plan_t plan, const floa
 extern "C" os_status oversketch_unsketch_rows(oversketch_plan_t plan, const float *U, int64_t l,
                                               int64_t ldu, uint64_t mask, float scale, void *dG,
                                               os_dtype g_t, int64_t ldg, void *stream) {
+    OSK_NVTX("unsketch_rows");
     return unsketch_rows_impl(reinterpret_cast<const Plan *>(plan), U, l, ldu, mask, scale, dG, g_t,
                               ldg, as_stream(stream));
 }

@@ -488,6 +488,7 @@ extern "C" os_status oversketch_sketch_left_sparse(oversketch_plan_t plan, const
                                                    int64_t lda, void *At, os_dtype out_t, int64_t ldat,
                                                    float *scales, const float *col_scale, uint64_t block_mask,
                                                    void *stream) {
+    OSK_NVTX("sketch_left_sparse");
     return sketch_left_sparse_impl(reinterpret_cast<const Plan *>(plan), A, a_t, m, lda, At, out_t, ldat, scales,
                                    col_scale, block_mask, as_stream(stream));
 }
