@@ -40,9 +40,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sketched A·B effective TFLOP/s (2mnl/t) vs exact GEMM at stated Frobenius error"
-# DRAM bytes (read + write) of one gemm_pair_bf16_kernel launch on the square workload,
-# from one ncu capture of this bench (profiles/square_launch_list.md)
-TRAFFIC_GEMM_PAIR_SQUARE = 4875390720 + 1055008512
+# DRAM bytes (read + write) of one gemm_pair_bf16_kernel launch on the square workload:
+# one ncu capture of the 8192 x 8192 x 8192 product (--shape 8192,65536,8192), scaled by
+# the 4x tiles of the full 16384 x 8192 x 16384 product (profiles/square_launch_list.md)
+TRAFFIC_GEMM_PAIR_SQUARE = 4 * (1283784448 + 254658304)
 UNIT = "TFLOP/s"
 
 
@@ -743,7 +744,8 @@ def run_hessian(args):
     world, rank, _ = _init_dist()
     build.build()
     peaks, peak_kind = _peaks()
-    w = W.HESSIAN
+    w = W.HESSIAN if not args.rows else W.scaled(W.HESSIAN, m=args.rows,
+                                                 name=f"hessian rows 0..{args.rows - 1} (profiling size)")
     offs, idx, val = w.left_sparse(range(w.m))
     A = torch.zeros((w.m, w.n), dtype=torch.float32, device="cuda")
     rows_of = torch.repeat_interleave(torch.arange(w.m, device="cuda"), torch.from_numpy(np.diff(offs)).cuda())
@@ -782,7 +784,7 @@ def run_hessian(args):
     err, cpu = None, None
     if _cpu_leg(args, rank, world):
         import oracle
-        rows = [0, 1, 777, 2048, 3333, 4095]
+        rows = [r for r in [0, 1, 777, 2048, 3333, 4095] if r < w.m]
         A_r = A[rows].cpu().numpy().astype(np.float64)
         h, s = oracle.hash_tables(w.n, w.b, w.N, w.e, w.hash_seed)
         if not args.no_check:
@@ -1133,6 +1135,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
     ap.add_argument("--recompute", action="store_true", help="autograd: recompute the sketches in backward")
     ap.add_argument("--dense-sketch", action="store_true", help="hessian: sketch A with the dense gather path")
+    ap.add_argument("--rows", type=int, default=0, help="hessian: the first ROWS rows of A only (profiling size)")
     ap.add_argument("--lp-iters", type=int, default=100,
                     help="lp: barrier iterations per run (0: time the Hessian at x = 0 only)")
     args = ap.parse_args()
