@@ -311,9 +311,10 @@ def run_ours(args):
     At, a_sc = ops.sketch_left(p, A, sd)
     BtT, b_sc = ops.sketch_right(p, B, sd)
     C = torch.empty((w.m, w.l), dtype=torch.float32, device=dev)
-    # one packed-strip workspace, reused by the left and then the right sketch (as oversketch_matmul does)
-    ws_pack = torch.empty(max(ops.sketch_workspace(p, w.m), ops.sketch_workspace(p, w.l)),
-                          dtype=torch.uint8, device=dev)
+    # one packed-strip workspace, reused by the left and then the right sketch (as oversketch_matmul does;
+    # FP8 sketches also stage their FP32 sums there)
+    ws_pack = torch.empty(ops.workspace_size(p, w.m, w.l, torch.float32, gd) if gd == "fp8" else
+                          max(ops.sketch_workspace(p, w.m), ops.sketch_workspace(p, w.l)), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     # the same three calls oversketch_matmul makes: only kept blocks are sketched
@@ -385,19 +386,21 @@ def run_ours(args):
     if not args.no_forms:
         for f in [x for x in ("f32", "fp8", "bf16") if x != gd]:
             sf = _sketch_dtype(f, w.b)
-            Af, asf = ops.sketch_left(p, A, sf, workspace=ws_pack)
-            Bf, bsf = ops.sketch_right(p, B, sf, workspace=ws_pack)
-            phases_f = [("sketch_left", lambda: ops.sketch_left(p, A, sf, out=Af, scales=asf, workspace=ws_pack,
+            # the workspace oversketch_matmul sizes for this dtype (FP8: room to stage the FP32 sums)
+            ws_f = torch.empty(ops.workspace_size(p, w.m, w.l, torch.float32, f), dtype=torch.uint8, device=dev)
+            Af, asf = ops.sketch_left(p, A, sf, workspace=ws_f)
+            Bf, bsf = ops.sketch_right(p, B, sf, workspace=ws_f)
+            phases_f = [("sketch_left", lambda: ops.sketch_left(p, A, sf, out=Af, scales=asf, workspace=ws_f,
                                                                  block_mask=w.mask)),
                         ("sketch_right", lambda: ops.sketch_right(p, B, sf, out=Bf, scales=bsf, block_mask=w.mask,
-                                                                   workspace=ws_pack)),
+                                                                   workspace=ws_f)),
                         ("gemm_masked", lambda: ops.gemm_masked(p, Af, Bf, w.mask, C=C, a_scales=asf, b_scales=bsf,
                                                                 dtype=sf))]
             ms_f, per_f, _ = _time_phases(phases_f, max(3, min(args.steps, 10)), 2, world, sample_clocks=False)
             forms[f] = {"ms_per_step": ms_f, "tflops": _job_value(2.0 * w.m * w.n * w.l, ms_f, world),
                         "phases_ms": {k_: round(v_, 4) for k_, v_ in per_f.items()},
                         "sketch_dtype": sf}
-            del Af, Bf, asf, bsf
+            del Af, Bf, asf, bsf, ws_f
         torch.cuda.synchronize()
 
     # ---- exact GEMM on the same GPU: the same tcgen05 kernel over K = n (all blocks kept) ----
@@ -866,6 +869,31 @@ def run_batched(args):
                                                                                       os.cpu_count() or 1)),
                "kind": "oracle", "sample": f"3x3 entries of C in products {sample}, hash tables, both "
                                            f"sketches and the masked product in FP64 (effective flop 2*3*n*3)"}
+    # the same products through oversketch_matmul_batched (caller workspace, masks read on
+    # the device): one captured graph replayed with two straggler sets
+    batch.close()
+    plans = [d[3] for d in dev]
+    As, Bs, Cs = [d[0] for d in dev], [d[1] for d in dev], [d[2] for d in dev]
+    masks = torch.tensor([d[4] for d in dev], dtype=torch.int64, device="cuda")
+    ws = torch.empty(ops.matmul_batched_workspace(plans, [m for m, _, _ in shapes], [n for _, n, _ in shapes],
+                                                  [l for _, _, l in shapes]), dtype=torch.uint8, device="cuda")
+    ops.matmul_batched(plans, As, Bs, Cs, masks, workspace=ws)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ops.matmul_batched(plans, As, Bs, Cs, masks, workspace=ws)
+    shifted = torch.tensor([0b11111 & ~(1 << ((q + 2) % 5)) for q in range(len(dev))], dtype=torch.int64,
+                           device="cuda")
+    ms_mb, per_mb, _ = _time_phases([("masks p mod 5", lambda: (masks.copy_(torch.tensor([d[4] for d in dev],
+                                                                                            dtype=torch.int64)),
+                                                                 g.replay())),
+                                     ("masks p+2 mod 5", lambda: (masks.copy_(shifted), g.replay()))],
+                                    max(2, args.steps // 2), 1, world, sample_clocks=False)
+    batched_entry = {"ms_per_run": ms_mb / 2, "phases_ms": {k_: round(v_, 3) for k_, v_ in per_mb.items()},
+                     "tflops": _job_value(flop_eff, ms_mb / 2, world), "workspace_bytes": ws.numel(),
+                     "what": "oversketch_matmul_batched captured once in a CUDA graph and replayed with two "
+                             "device-resident straggler sets (every block sketched, dropped blocks' CTAs return at once)"}
+    del ws
     cfg = {"workload": "batched: 256 uneven products, m,l ~ U[256,4096], n log-U[8192,131072], b=n/32, N=4, e=1, "
                        "product p drops block p mod 5", "count": 256,
            "input_bytes": sum((m + l) * n * 4 for m, n, l in shapes), "gemm_dtype": "bf16", "input_dtype": "f32",
@@ -873,10 +901,9 @@ def run_batched(args):
            "graph": {k_: v_ for k_, v_ in info.items()}, "create_s": round(t_create, 2)}
     line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, cpu, None,
                  info["kernel_launches"] * args.steps, clk, err, world,
-                 gemm={"flop_per_run": gemm_flop})
+                 gemm={"flop_per_run": gemm_flop}, matmul_batched=batched_entry)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    batch.close()
     return 0
 
 

@@ -154,7 +154,12 @@ OS_API os_status oversketch_sketch_size(double eps, double theta, int32_t b, dou
  *     128t .. 128t+127) of row r are all <= 448 * 2^e_rt in magnitude (1.0
  *     for an all-zero slice); At holds round-to-nearest-even, saturating E4M3
  *     codes of (sum / 2^e_rt).  Entries of padding rows are not written.
- *     NULL otherwise.  FP8 needs b % 128 == 0.
+ *     NULL otherwise.  FP8 needs b % 128 == 0.  When the workspace also has
+ *     room for m x z FP32 values after the regular workspace (ws_bytes >=
+ *     roundup256(oversketch_sketch_workspace(plan, m, a_t)) + 4*m*z + 256), the
+ *     FP32 sums are staged there and quantised by a second kernel instead of in
+ *     the gather's epilogue (thread-block clusters of four): the same codes and
+ *     scales, faster.
  *   Sums are accumulated in FP32 in ascending order of i inside a bucket;
  *   BF16 output is the round-to-nearest-even of that FP32 sum.
  *   block_mask: bit j set = compute the columns of block j; 0 = all blocks.
@@ -451,16 +456,13 @@ OS_API os_status oversketch_test_wait_timeout(uint64_t limit_ns, int32_t skip_kb
  *     accumulation); col_scale, symmetric and flags are not supported here.
  *   workspace: device memory of oversketch_matmul_batched_workspace_size bytes:
  *     the GEMM descriptors, every product's BF16 sketches ((m_p + l_p) z_p
- *     elements) and eight packing slots.  The call allocates nothing: the
+ *     elements) and one packing slot.  The call allocates nothing: the
  *     descriptors are written into the workspace by kernels that carry them as
  *     launch parameters, so a captured graph holds everything it needs.
- * Work: the descriptors, then the sketches on eight streams forked from `stream`
+ * Work, all on `stream`: the descriptors, the sketches product after product
  * (every block is sketched; CTAs of blocks the device mask drops return at
  * once), then one persistent tcgen05 launch over the tiles of all products
- * (longest sketch first), joined back on `stream`.  The sketch streams and
- * their events belong to the library, one set per device, created on the first
- * call (make it before any capture); calls from several host threads are
- * enqueued one at a time.
+ * (longest sketch first).
  * Errors: OS_ERR_INVALID_ARG, OS_ERR_DTYPE, OS_ERR_UNSUPPORTED, OS_ERR_WORKSPACE,
  * OS_ERR_CUDA.
  */
@@ -489,8 +491,7 @@ OS_API os_status oversketch_matmul_batched(int32_t count, const oversketch_plan_
  * elements per product) and W workspace slots of the largest single-product
  * packing size, W <= workspace_limit / slot (0: 16 GiB).  tune != 0 times a
  * few (W, tile width) choices on `stream` (running the products several
- * times) and keeps the fastest; tune == 0 takes W = min(8, ...) and 256-wide
- * tiles.  Synchronous; call it outside any stream capture.
+ * times) and keeps the fastest; tune == 0 takes W = 1 and 256-wide tiles.  Synchronous; call it outside any stream capture.
  *   problems: host array of count (1..1024) descriptors; A_p, B_p device
  *     row-major in a_t / b_t (OS_F32 or OS_BF16), C_p device FP32; every plan
  *     on the current device with b % 64 == 0; m_p, n_p, l_p >= 1.

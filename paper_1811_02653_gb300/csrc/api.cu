@@ -11,6 +11,7 @@ namespace osk {
 
 // implemented in sketch.cu / sketch_sparse.cu / gemm_simt.cu / gemm_tc.cu
 size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t);
+size_t fp8_staging_bytes(const Plan *p, int64_t F);
 os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m, int64_t lda,
                            void *At, os_dtype out_t, int64_t ldat, float *scales,
                            const float *col_scale, uint64_t block_mask, void *ws, size_t ws_bytes,
@@ -92,9 +93,14 @@ MatmulLayout layout(const Plan *p, int64_t m, int64_t l, os_dtype a_t, os_dtype 
     L.bt_bytes = sym ? 0 : align256((size_t)l * L.ldbt * es * planes);
     L.as_bytes = g == OS_FP8E4M3 ? align256((size_t)fp8_scale_ld(m) * L.nsl * 4) : 0;
     L.bs_bytes = (g == OS_FP8E4M3 && !sym) ? align256((size_t)fp8_scale_ld(l) * L.nsl * 4) : 0;
-    // the packed-strip buffer is reused by the left and then the right sketch
-    const size_t wl = sketch_workspace_bytes(p, m, a_t);
-    const size_t wr = sym ? 0 : sketch_workspace_bytes(p, l, b_t);
+    // the packed-strip buffer is reused by the left and then the right sketch; FP8
+    // sketches stage their FP32 sums after it and quantise them in a second pass
+    size_t wl = sketch_workspace_bytes(p, m, a_t);
+    size_t wr = sym ? 0 : sketch_workspace_bytes(p, l, b_t);
+    if (g == OS_FP8E4M3) {
+        wl = align256(wl) + fp8_staging_bytes(p, m);
+        if (!sym) wr = align256(wr) + fp8_staging_bytes(p, l);
+    }
     L.left_ws = align256(wl > wr ? wl : wr);
     return L;
 }

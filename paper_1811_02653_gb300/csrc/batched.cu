@@ -18,7 +18,6 @@
 // and keep the fastest graph.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -277,11 +276,13 @@ os_status create(const os_problem *problems, int32_t count, os_dtype a_t, os_dty
     OSK_TRY(gemm_grouped_prepare());
     // candidates: (branches, tile); without tuning the first one
     std::vector<std::pair<int, GroupTile>> cand;
-    const int wdef = std::min(B->max_branches, 8);
+    // one branch by default: concurrent branches' strips compete for L2 (the tuner
+    // picked one branch on the 256-product workload)
+    const int wdef = 1;
     cand.push_back({wdef, kGroupBN256});
     if (tune) {
         cand.push_back({wdef, kGroupBN128});
-        for (int w : {1, 4, 16})
+        for (int w : {2, 4, 8})
             if (w <= B->max_branches && w != wdef) {
                 cand.push_back({w, kGroupBN256});
                 cand.push_back({w, kGroupBN128});
@@ -319,12 +320,13 @@ os_status create(const os_problem *problems, int32_t count, os_dtype a_t, os_dty
 // The batched product with a caller-owned workspace and run-time masks
 // (oversketch_matmul_batched).  Each call: the GEMM descriptors are written into
 // the workspace by small kernels that carry them as launch parameters (so a
-// captured graph holds them by value), the sketches run on kBranches forked
-// streams (every block is sketched; CTAs of blocks that the device mask drops
-// return at once), then one grouped tcgen05 launch reads each product's mask
-// from device memory for its K list and its 1/k.  Nothing is allocated.
+// captured graph holds them by value), the sketches of the products run one
+// after another on the caller's stream (every block is sketched; CTAs of blocks
+// that the device mask drops return at once), then one grouped tcgen05 launch
+// reads each product's mask from device memory for its K list and its 1/k.
+// Nothing is allocated.  (Sketching products concurrently on parallel branches
+// measured slower: their strips compete for L2.)
 
-constexpr int kBranches = 8;
 constexpr int kDescPerChunk = 40;
 
 struct DescChunk {
@@ -371,35 +373,7 @@ os_status batched_layout(int32_t count, const oversketch_plan_t *plans, const in
     }
     L->operands = off;
     L->slot = align256(slot);
-    const int W = std::min(kBranches, (int)count);
-    L->total = L->desc + L->operands + (size_t)W * L->slot + 256;
-    return OS_OK;
-}
-
-// Streams the sketches of a call fork onto, and the events of the fork and the
-// joins (one set per device, created on the first call; no event or stream is
-// created or destroyed while a stream may be capturing).  The lock serialises
-// the enqueueing of calls from several host threads on one device.
-struct Branches {
-    cudaStream_t stream[kBranches];
-    cudaEvent_t fork, join[kBranches];
-    std::mutex mu;
-};
-
-os_status branches_of(int dev, Branches **out) {
-    static Branches br[64];
-    static std::mutex mu;
-    if (dev < 0 || dev >= 64) return OS_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(mu);
-    Branches &b = br[dev];
-    if (!b.fork) {
-        for (int w = 0; w < kBranches; ++w) {
-            OSK_CUDA_TRY(cudaStreamCreateWithFlags(&b.stream[w], cudaStreamNonBlocking));
-            OSK_CUDA_TRY(cudaEventCreateWithFlags(&b.join[w], cudaEventDisableTiming));
-        }
-        OSK_CUDA_TRY(cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming));
-    }
-    *out = &b;
+    L->total = L->desc + L->operands + L->slot + 256;
     return OS_OK;
 }
 
@@ -433,7 +407,7 @@ extern "C" os_status oversketch_matmul_batched(int32_t count, const oversketch_p
     if (!A || !B || !C || !masks) return OS_ERR_INVALID_ARG;
     int dev = 0;
     OSK_CUDA_TRY(cudaGetDevice(&dev));
-    std::vector<int> live;
+    std::vector<int> live;   // products with a non-empty C
     for (int i = 0; i < count; ++i) {
         const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
         if (p->device != dev) return OS_ERR_INVALID_ARG;
@@ -481,39 +455,15 @@ extern "C" os_status oversketch_matmul_batched(int32_t count, const oversketch_p
         upload_groups_kernel<<<1, 256, 0, st>>>(chunk, desc);
         OSK_TRY(check_launch());
     }
-    // sketches on forked streams, heaviest first, greedy by work
-    Branches *br = nullptr;
-    OSK_TRY(branches_of(dev, &br));
-    const int W = std::min(kBranches, cnt);
-    std::vector<int> sk = live;
-    auto work = [&](int i) { return (m[i] + l[i]) * n[i]; };
-    std::stable_sort(sk.begin(), sk.end(), [&](int x, int y) { return work(x) > work(y); });
-    std::vector<int64_t> load(W, 0);
-    std::vector<std::vector<int>> branch(W);
-    for (int i : sk) {
-        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        branch[w].push_back(i);
-        load[w] += work(i);
-    }
-    {
-        std::lock_guard<std::mutex> lock(br->mu);
-        OSK_CUDA_TRY(cudaEventRecord(br->fork, st));
-        for (int w = 0; w < W; ++w) {
-            cudaStream_t bs = br->stream[w];
-            OSK_CUDA_TRY(cudaStreamWaitEvent(bs, br->fork, 0));
-            void *ws = slots + (size_t)w * L.slot;
-            for (int i : branch[w]) {
-                const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
-                const int64_t z = (int64_t)p->P * p->b;
-                const uint64_t all = p->P >= 64 ? ~0ull : ((1ull << p->P) - 1ull);
-                OSK_TRY(sketch_left_impl(p, A[i], a_t, m[i], n[i], ops_base + L.at_off[i], OS_BF16, z, nullptr, nullptr,
-                                         all, ws, L.slot, bs, masks + i));
-                OSK_TRY(sketch_right_impl(p, B[i], b_t, l[i], l[i], ops_base + L.bt_off[i], OS_BF16, z, nullptr, all, ws,
-                                          L.slot, bs, nullptr, masks + i));
-            }
-            OSK_CUDA_TRY(cudaEventRecord(br->join[w], bs));
-            OSK_CUDA_TRY(cudaStreamWaitEvent(st, br->join[w], 0));
-        }
+    // the sketches, one product after another, sharing one packing slot
+    for (int i : live) {
+        const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
+        const int64_t z = (int64_t)p->P * p->b;
+        const uint64_t all = p->P >= 64 ? ~0ull : ((1ull << p->P) - 1ull);
+        OSK_TRY(sketch_left_impl(p, A[i], a_t, m[i], n[i], ops_base + L.at_off[i], OS_BF16, z, nullptr, nullptr, all,
+                                 slots, L.slot, st, masks + i));
+        OSK_TRY(sketch_right_impl(p, B[i], b_t, l[i], l[i], ops_base + L.bt_off[i], OS_BF16, z, nullptr, all, slots,
+                                  L.slot, st, nullptr, masks + i));
     }
     return gemm_grouped_bf16(desc, cnt, tiles, kGroupBN256, st);
 }

@@ -565,6 +565,46 @@ os_status launch_entry_weights(const Plan *p, const float *s, uint64_t block_mas
     return check_launch();
 }
 
+// FP8 codes and UE8M0 scales from FP32 sums staged in global memory: one warp per
+// (row, 128-column slice of a listed block); the same rule as the gather's fused
+// FP8 epilogue (smallest e with amax <= 448 * 2^e, codes = RNE(x / 2^e)), so the
+// codes and scales are the same bits.
+__global__ void __launch_bounds__(256) quantize_fp8_kernel(const float *__restrict__ Y, int64_t ldy, int64_t rows,
+                                                           int32_t b, BlockList blocks,
+                                                           __nv_fp8_e4m3 *__restrict__ Q, int64_t ldq,
+                                                           float *__restrict__ scales, int64_t lds) {
+    const int lane = threadIdx.x & 31;
+    const int64_t per_row = (int64_t)blocks.count * (b / 128);
+    const int64_t total = rows * per_row;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t r = w / per_row;
+        const int s = (int)(w - r * per_row);
+        const int bt = s / (b / 128);
+        const int64_t q0 = (int64_t)blocks.idx[bt] * b + (int64_t)(s - bt * (b / 128)) * 128;
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(Y + r * ldy + q0) + lane);
+        float a = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        const int e = fp8_scale_exponent(a);
+        const float inv = ldexpf(1.f, -e);
+        __nv_fp8_e4m3 c[4] = {__nv_fp8_e4m3(v.x * inv), __nv_fp8_e4m3(v.y * inv), __nv_fp8_e4m3(v.z * inv),
+                              __nv_fp8_e4m3(v.w * inv)};
+        *reinterpret_cast<uint32_t *>(Q + r * ldq + q0 + 4 * lane) = *reinterpret_cast<const uint32_t *>(c);
+        if (lane == 0) scales[(q0 / 128) * lds + r] = ldexpf(1.f, e);   // slice-major
+    }
+}
+
+os_status launch_quantize_fp8(const Plan *p, const float *Y, int64_t ldy, int64_t rows, uint64_t block_mask,
+                              void *Q, int64_t ldq, float *scales, int64_t lds, cudaStream_t st) {
+    const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
+    const int64_t warps = rows * blocks.count * (p->b / 128);
+    const int64_t ctas = (warps + 7) / 8;
+    quantize_fp8_kernel<<<(unsigned)(ctas < 152 * 16 ? ctas : 152 * 16), 256, 0, st>>>(
+        Y, ldy, rows, p->b, blocks, (__nv_fp8_e4m3 *)Q, ldq, scales, lds);
+    return check_launch();
+}
+
 template <typename InT, typename OutT, int QT, int SLOTS>
 os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int64_t ldx, int64_t F,
                           const float *wts, void *Yt, int64_t ldy, float *scales, int64_t scale_ld,
@@ -716,6 +756,20 @@ size_t sketch_workspace_bytes(const Plan *p, int64_t F, os_dtype in_t) {
     return ws_align(strip_bytes(p, F, in_t)) + (size_t)p->P * p->pstride * sizeof(float) + 256;
 }
 
+// FP8 output staged in FP32: a workspace this much larger (F x z FP32 sums after the
+// regular workspace) lets the sketch gather FP32 sums without clusters and quantise
+// them in a second pass (same codes and scales as the fused FP8 epilogue).
+size_t fp8_staging_bytes(const Plan *p, int64_t F) { return (size_t)F * (size_t)p->P * p->b * sizeof(float) + 256; }
+
+namespace {
+float *fp8_staging(const Plan *p, void *ws, size_t ws_bytes, int64_t F, os_dtype in_t) {
+    const size_t off = ws_align(sketch_workspace_bytes(p, F, in_t));
+    if (!ws || ws_bytes < off + fp8_staging_bytes(p, F)) return nullptr;
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(ws) + off + 255) & ~uintptr_t(255);
+    return reinterpret_cast<float *>(a);
+}
+}  // namespace
+
 namespace {
 void *ws_base(void *ws) {
     return reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
@@ -757,6 +811,14 @@ os_status sketch_left_impl(const Plan *p, const void *A, os_dtype a_t, int64_t m
     OSK_TRY(sketch_left_check(p, A, a_t, m, lda, At, out_t, ldat, scales, block_mask));
     if (m == 0) return OS_OK;
     if (!ws || ws_bytes < sketch_workspace_bytes(p, m, a_t)) return OS_ERR_WORKSPACE;
+    if (out_t == OS_FP8E4M3 && !dmask) {
+        if (float *stg = fp8_staging(p, ws, ws_bytes, m, a_t)) {
+            const int64_t z = (int64_t)p->P * p->b;
+            OSK_TRY(sketch_left_impl(p, A, a_t, m, lda, stg, OS_F32, z, nullptr, col_scale, block_mask, ws, ws_bytes,
+                                     st, dmask));
+            return launch_quantize_fp8(p, stg, z, m, block_mask, At, ldat, scales, fp8_scale_ld(m), st);
+        }
+    }
     void *Xs = ws_base(ws);
     const float *wts = nullptr;
     OSK_TRY(make_weights(p, col_scale, block_mask, ws_weights(p, ws, m, a_t), &wts, st));
@@ -782,6 +844,14 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
     OSK_TRY(check_out(p, l, BtT, out_t, ldbt, scales));
     if (l == 0) return OS_OK;
     if (!B) return OS_ERR_INVALID_ARG;
+    if (out_t == OS_FP8E4M3 && !dmask) {
+        if (float *stg = fp8_staging(p, ws, ws_bytes, l, b_t)) {
+            const int64_t z = (int64_t)p->P * p->b;
+            OSK_TRY(sketch_right_impl(p, B, b_t, l, ldb, stg, OS_F32, z, nullptr, block_mask, ws, ws_bytes, st,
+                                      row_scale, dmask));
+            return launch_quantize_fp8(p, stg, z, l, block_mask, BtT, ldbt, scales, fp8_scale_ld(l), st);
+        }
+    }
     // FP32 input with 16-byte aligned rows: gather whole 128-wide strips in place,
     // and pack only a ragged remainder of fewer than 128 columns.
     const bool direct = b_t == OS_F32 && aligned16(B) && ldb % 4 == 0 && ldb * 4 < (int64_t(1) << 32) &&

@@ -229,6 +229,38 @@ def test_sketch_fp8_parity(ops, m, n, l, b, N, e):
     assert_fp8_within(BtT.float().cpu().numpy(), ops.fp8_scales_by_row(sb, l).cpu().numpy(), ref_r.T, bd_r.T)
 
 
+@pytest.mark.parametrize("m,n,l,b,N,e,mask", [(300, 4000, 260, 128, 3, 1, 0b1011),   # packed right remainder
+                                               (130, 9000, 384, 256, 2, 2, 0)])        # right in place
+def test_sketch_fp8_staged_equals_fused(ops, m, n, l, b, N, e, mask):
+    # with room for F x z FP32 sums after the regular workspace the FP8 sketch stages
+    # the sums and quantises them in a second pass; codes and scales are the fused
+    # epilogue's bits, and within the oracle's FP8 windows
+    rng = np.random.default_rng(m + l)
+    A = (rng.standard_normal((m, n)) * np.exp(rng.standard_normal((m, 1)) * 3)).astype(np.float32)
+    B = rng.standard_normal((n, l)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 5)
+    h, s = oracle.hash_tables(n, b, N, e, 5)
+    z = (N + e) * b
+    for X, fn, rows in ((A, ops.sketch_left, m), (B, ops.sketch_right, l)):
+        base = ops.sketch_workspace(p, rows)
+        big = torch.empty((base + 255) // 256 * 256 + rows * z * 4 + 256, dtype=torch.uint8, device="cuda")
+        fused, sf = fn(p, _dev(X), "fp8", block_mask=mask)
+        staged, ss = fn(p, _dev(X), "fp8", block_mask=mask, workspace=big)
+        cols = torch.from_numpy(oracle.selected_columns(mask or (1 << (N + e)) - 1, N + e, b)).cuda()
+        sl = torch.from_numpy(np.unique(oracle.selected_columns(mask or (1 << (N + e)) - 1, N + e, b) // 128)).cuda()
+        assert torch.equal(fused.view(torch.uint8)[:, cols], staged.view(torch.uint8)[:, cols])
+        assert torch.equal(sf[sl, :rows], ss[sl, :rows])
+        if fn is ops.sketch_left:
+            ref, bd = sketch_bounds_left(A, h, s, b)
+        else:
+            ref, bd = sketch_bounds_right(B, h, s, b)
+            ref, bd = ref.T, bd.T
+        c = cols.cpu().numpy()
+        scale_rows = ops.fp8_scales_by_row(ss, rows).cpu().numpy()
+        slices = c.reshape(-1, 128)[:, 0] // 128
+        assert_fp8_within(staged.float().cpu().numpy()[:, c], scale_rows[:, slices], ref[:, c], bd[:, c])
+
+
 def test_sketch_argument_errors(ops):
     p = ops.plan(1000, 100, 2, 1, 0)          # b = 100: FP8 needs b % 128 == 0
     A = torch.zeros((4, 1000), device="cuda")
