@@ -529,7 +529,8 @@ def run_ours(args):
             "roofline": roof, "sketch_rooflines": sketch_roofs, "cpu_baseline": cpu,
             "e2e": {"value": _job_value(flop_eff, e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 4 * args.steps, "clocks": clk, "error": err, "exact_gemm": exact,
+            # pack + gather (left), gather (right), GEMM; FP8 adds the two quantisation passes
+            "gpu_launches": (6 if sd == "fp8" else 4) * args.steps, "clocks": clk, "error": err, "exact_gemm": exact,
             "forms": forms,
             "plan_ms": _plan_record(plan_s, plan_dev)}
     if rank == 0:
