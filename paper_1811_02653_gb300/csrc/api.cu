@@ -293,7 +293,9 @@ HostPlan host_plan(const Plan *p, int64_t m, int64_t l, os_dtype a_t, os_dtype b
     const bool sym = o && o->symmetric;
     const size_t ea = dtype_size(a_t), eb = dtype_size(b_t);
     h.lda_d = round_up(p->n, (int64_t)(16 / ea));
-    h.ldb_d = round_up(l, (int64_t)(16 / eb));
+    // FP32 B keeps the pitch of a contiguous device tensor (l), so its right sketch
+    // takes the same in-place path as the device entry point on that tensor
+    h.ldb_d = b_t == OS_F32 ? l : round_up(l, (int64_t)(16 / eb));
     h.ldc_d = round_up(l, 4);
     h.a_bytes = align256((size_t)m * h.lda_d * ea);
     h.b_bytes = sym ? 0 : align256((size_t)p->n * h.ldb_d * eb);

@@ -12,11 +12,15 @@
 //
 // The gather reads X in strips of W free indices (W = 128 for FP32, 256 for
 // BF16): strip s holds X[0..n-1, Ws .. Ws+W-1], and a random row of it is one
-// 512-byte piece, 16 bytes per lane of a warp.  The left operand (and a right operand whose rows are not 16-byte
-// aligned) is first packed strip-major into the workspace, n contiguous rows
-// of 128 elements per strip, zero-padded past the free extent; packing the
-// left operand is the transpose it needs anyway.  An aligned FP32 right
-// operand is gathered in place.  Whole 512-byte pieces keep the address
+// 512-byte piece, 16 bytes per lane of a warp.  The left operand (and a BF16
+// right operand) is first packed strip-major into the workspace, n contiguous
+// rows of 128 elements per strip, zero-padded past the free extent; packing
+// the left operand is the transpose it needs anyway.  An FP32 right operand
+// is gathered in place: in 128-wide strips when its rows are 16-byte aligned,
+// else in 124-wide strips whose row pieces start d = 0..3 elements into a
+// 16-byte granule (lane c loads granule c; the sums are kept per class d and
+// realigned with one shuffle per bucket), or packed when that costs less
+// (more than 6 blocks gathered).  Whole 512-byte pieces keep the address
 // translations of the random row accesses cheap; 128-byte pieces spread over
 // a 4 GB matrix ran at a quarter to a half of the L2 gather rate on GB300.
 //
@@ -116,8 +120,8 @@ __device__ __align__(16) float g_zero_row[8];
 // members s, s+SLOTS, ... of a bucket in ascending order and the partial sums
 // are combined by a fixed butterfly (one chain when SLOTS = 1): a fixed order,
 // so the results are bitwise reproducible.
-template <typename InT, typename OutT, int QT, bool kScale, int SLOTS>
-__global__ void __launch_bounds__(kWarps * 32, 4)
+template <typename InT, typename OutT, int QT, bool kScale, int SLOTS, bool kMis>
+__global__ void __launch_bounds__(kWarps * 32, kMis ? 3 : 4)
 sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ldx, int64_t F,
                      const uint32_t *__restrict__ pperm, const uint32_t *__restrict__ poffs,
                      int64_t pstride, int32_t b, int32_t z, const float *__restrict__ wts,
@@ -126,8 +130,11 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                      const uint64_t *__restrict__ dmask) {
     constexpr int SUBS = 32 / SLOTS;     // lanes per member
     constexpr int VW = 16 / (int)sizeof(InT);   // free indices per lane: 16 bytes
-    constexpr int TF = VW * SUBS;        // free indices per CTA (one strip)
+    constexpr int TF = VW * SUBS;        // free indices per tile row (one strip)
+    constexpr int TFO = kMis ? TF - 4 : TF;   // free indices written per CTA
     constexpr int PITCH = TF + 1;        // odd pitch: conflict-free column reads
+    constexpr int NC = kMis ? 4 : 1;     // accumulator sets: one per misalignment class
+    static_assert(!kMis || (std::is_same<InT, float>::value && SLOTS == 1), "misaligned rows: FP32, one member per load");
     constexpr int G = 2 * SLOTS;         // groups of 4 members per batch: 8 loads per lane in flight
     constexpr int QPW = QT / kWarps;     // buckets per warp
     static_assert(QT == 8 || QT == 16 || QT == 32 || QT == 128, "tile of 8, 16, 32 or 128 sketched columns");
@@ -141,7 +148,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
     const int jblk = blocks.idx[bt];
     const int q0 = jblk * b + (blockIdx.x - bt * tiles_per_block) * QT;
     const int qend = min(z, jblk * b + b);
-    const int64_t f0 = (int64_t)blockIdx.y * TF;
+    const int64_t f0 = (int64_t)blockIdx.y * TFO;
     // a block mask read at run time: CTAs of blocks it does not keep have nothing to do
     if (dmask && !((__ldg(dmask) >> jblk) & 1ull)) return;
     using L = Loader<InT, VW, true>;
@@ -177,6 +184,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
             constexpr int KS = 4 * GG / SLOTS;            // member loads per lane
             uint4 v[KS];
             float wgt[KS];
+            uint32_t cls = 0;                             // 4 x misalignment class of member k: bits 2k+2, 2k+3
 #pragma unroll
             for (int k = 0; k < KS; ++k) {
                 const uint32_t ent = __shfl_sync(0xffffffffu, e, k * SLOTS + slot);
@@ -186,26 +194,73 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                 } else {
                     wgt[k] = __uint_as_float(0x3f800000u | (ent & kSignBit));
                 }
-                const uint64_t addr = (uint64_t)(ent & kIndexMask) * row_bytes + xbase;
+                uint64_t addr = (uint64_t)(ent & kIndexMask) * row_bytes + xbase;
+                if constexpr (kMis) {
+                    // The row piece starts d = 0..3 elements into a 16-byte granule
+                    // (the same d on every lane); lane c loads granule c from there:
+                    // the 32 granules cover the strip's 124 elements and end inside
+                    // the row (the launch keeps 128 elements of every strip in it).
+                    cls |= ((uint32_t)addr & 12u) << (2 * k);
+                    addr &= ~uint64_t(15);
+                }
                 v[k] = L::load_raw(reinterpret_cast<const InT *>(ent != kPadEntry ? addr : zrow));
             }
 #pragma unroll
             for (int k = 0; k < KS; ++k) {
                 float x[VW];
                 L::unpack(v[k], x);
+                if constexpr (kMis) {
+                    // one accumulator set per class (a warp-uniform branch)
+                    const uint32_t d = (cls >> (2 * k)) & 12u;
+                    if (d == 0u) {
 #pragma unroll
-                for (int w = 0; w < VW; ++w) acc[w] = fmaf(wgt[k], x[w], acc[w]);
+                        for (int w = 0; w < VW; ++w) acc[w] = fmaf(wgt[k], x[w], acc[w]);
+                    } else if (d == 4u) {
+#pragma unroll
+                        for (int w = 0; w < VW; ++w) acc[VW + w] = fmaf(wgt[k], x[w], acc[VW + w]);
+                    } else if (d == 8u) {
+#pragma unroll
+                        for (int w = 0; w < VW; ++w) acc[2 * VW + w] = fmaf(wgt[k], x[w], acc[2 * VW + w]);
+                    } else {
+#pragma unroll
+                        for (int w = 0; w < VW; ++w) acc[3 * VW + w] = fmaf(wgt[k], x[w], acc[3 * VW + w]);
+                    }
+                } else {
+#pragma unroll
+                    for (int w = 0; w < VW; ++w) acc[w] = fmaf(wgt[k], x[w], acc[w]);
+                }
             }
         };
         auto flush = [&](int t, float *acc) {
+            float out[VW];
+            if constexpr (kMis) {
+                // class d holds element 4*sub + w - d of the strip in lane sub, slot w:
+                // free index 4*sub + w is slot w + d of this lane, or slot w + d - 4
+                // of the next lane; the classes are added in the order 0, 1, 2, 3
+                float nx[NC * VW];
 #pragma unroll
-            for (int w = 0; w < VW; ++w) {
-                if constexpr (SLOTS == 4) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], 8);
-                if constexpr (SLOTS >= 2) acc[w] += __shfl_xor_sync(0xffffffffu, acc[w], 16);
+                for (int d = 1; d < NC; ++d)
+#pragma unroll
+                    for (int w = 0; w < d; ++w) nx[d * VW + w] = __shfl_down_sync(0xffffffffu, acc[d * VW + w], 1);
+#pragma unroll
+                for (int w = 0; w < VW; ++w) {
+                    float o = acc[w];
+#pragma unroll
+                    for (int d = 1; d < NC; ++d)
+                        o += (w + d < VW) ? acc[d * VW + (w + d) % VW] : nx[d * VW + (w + d) % VW];
+                    out[w] = o;
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < VW; ++w) {
+                    out[w] = acc[w];
+                    if constexpr (SLOTS == 4) out[w] += __shfl_xor_sync(0xffffffffu, out[w], 8);
+                    if constexpr (SLOTS >= 2) out[w] += __shfl_xor_sync(0xffffffffu, out[w], 16);
+                }
             }
             if (slot == 0) {
 #pragma unroll
-                for (int w = 0; w < VW; ++w) tile[(warp * QPW + t) * PITCH + VW * sub + w] = acc[w];
+                for (int w = 0; w < VW; ++w) tile[(warp * QPW + t) * PITCH + VW * sub + w] = out[w];
             }
         };
 
@@ -226,9 +281,9 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
         };
         for (int t = 0; t < nb; ++t) {
             const uint32_t gE = __shfl_sync(0xffffffffu, gbl, t + 1);
-            float acc[VW];
+            float acc[NC * VW];
 #pragma unroll
-            for (int w = 0; w < VW; ++w) acc[w] = 0.f;
+            for (int w = 0; w < NC * VW; ++w) acc[w] = 0.f;
             while (gE - g >= (uint32_t)G) step(std::integral_constant<int, G>(), acc);
             const uint32_t r = gE - g;   // < G
             if constexpr (G >= 8) if (r & 4u) step(std::integral_constant<int, 4>(), acc);
@@ -262,7 +317,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
             a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 1));
             a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, 2));
             a = __shfl_sync(0xffffffffu, a, 0);
-            if (frow < F) {
+            if (ff < TFO && frow < F) {
                 const int e = fp8_scale_exponent(a);
                 const float inv = ldexpf(1.f, -e);
                 Yt[frow * ldy + q0 + lane] = __nv_fp8_e4m3(tile[lane * PITCH + ff] * inv);   // RNE, saturating
@@ -280,7 +335,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
                 const int ff = warp * (TF / kWarps) + t + rr;
                 const int64_t frow = f0 + ff;
                 const int q = q0 + qq;
-                if (frow < F && q < qend) {
+                if (ff < TFO && frow < F && q < qend) {
                     const float v = tile[qq * PITCH + ff];
                     OutT *dst = Yt + frow * ldy + q;
                     if constexpr (std::is_same<OutT, Tf32Pair>::value) {
@@ -301,7 +356,7 @@ sketch_gather_kernel(const InT *__restrict__ X, int64_t strip_stride, int64_t ld
         for (int t = 0; t < TF / kWarps; ++t) {
             const int ff = warp * (TF / kWarps) + t;
             const int64_t frow = f0 + ff;
-            if (frow >= F) break;
+            if (ff >= TFO || frow >= F) break;
             float v[VPL];
 #pragma unroll
             for (int k = 0; k < VPL; ++k) v[k] = tile[(lane + 32 * k) * PITCH + ff];
@@ -605,7 +660,7 @@ os_status launch_quantize_fp8(const Plan *p, const float *Y, int64_t ldy, int64_
     return check_launch();
 }
 
-template <typename InT, typename OutT, int QT, int SLOTS>
+template <typename InT, typename OutT, int QT, int SLOTS, bool kMis = false>
 os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int64_t ldx, int64_t F,
                           const float *wts, void *Yt, int64_t ldy, float *scales, int64_t scale_ld,
                           const BlockList &blocks, cudaStream_t st, int64_t plane_elems = 0,
@@ -613,11 +668,12 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
     const int z = p->P * p->b;
     const int tpb = (p->b + QT - 1) / QT;
     constexpr int TF = strip_of<InT>() / SLOTS;
-    dim3 grid((unsigned)(tpb * blocks.count), (unsigned)((F + TF - 1) / TF));
+    constexpr int TFO = kMis ? TF - 4 : TF;   // free indices written per CTA
+    dim3 grid((unsigned)(tpb * blocks.count), (unsigned)((F + TFO - 1) / TFO));
     if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;
     const size_t smem = sizeof(float) * QT * (TF + 1);
-    auto k = wts ? sketch_gather_kernel<InT, OutT, QT, true, SLOTS>
-                       : sketch_gather_kernel<InT, OutT, QT, false, SLOTS>;
+    auto k = wts ? sketch_gather_kernel<InT, OutT, QT, true, SLOTS, kMis>
+                       : sketch_gather_kernel<InT, OutT, QT, false, SLOTS, kMis>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if constexpr (sizeof(OutT) == 1) {
         // clusters of the 4 CTAs of a 128-column scale slice (b % 128 == 0, so
@@ -677,24 +733,30 @@ os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *wt
 
 // Gather straight from a row-major FP32 operand in 128-wide strips (512-byte row
 // pieces: one address translation per 512 bytes is cheap enough that no
-// packing pass is needed).  F must be a multiple of 128.
+// packing pass is needed).  F must be a multiple of 128.  With kMis the rows
+// need only 4-byte alignment: strips are 124 wide, each lane loads the 16-byte
+// granule holding its first element, and the sums are kept per misalignment
+// class and realigned once per bucket (F a multiple of 124).
+template <bool kMis>
 os_status launch_gather_direct(const Plan *p, const float *X, int64_t ldx, int64_t F, const float *wts,
                                void *Yt, os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld,
                                uint64_t block_mask, cudaStream_t st, int64_t plane_rows = 0,
                                const uint64_t *dmask = nullptr) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
-        switch (out_t) {
+    constexpr int64_t ss = kMis ? kStrip - 4 : kStrip;
+    switch (out_t) {
         case OS_F32:
-            return launch_gather_t<float, float, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld, blocks, st, 0, dmask);
+            return launch_gather_t<float, float, kGatherQT, 1, kMis>(p, X, ss, ldx, F, wts, Yt, ldy, nullptr,
+                                                                    scale_ld, blocks, st, 0, dmask);
         case OS_BF16:
-            return launch_gather_t<float, __nv_bfloat16, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld,
-                                                                blocks, st, 0, dmask);
+            return launch_gather_t<float, __nv_bfloat16, kGatherQT, 1, kMis>(p, X, ss, ldx, F, wts, Yt, ldy, nullptr,
+                                                                            scale_ld, blocks, st, 0, dmask);
         case OS_FP8E4M3:
-            return launch_gather_t<float, __nv_fp8_e4m3, 32, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, scales, scale_ld,
-                                                                 blocks, st, 0, dmask);
+            return launch_gather_t<float, __nv_fp8_e4m3, 32, 1, kMis>(p, X, ss, ldx, F, wts, Yt, ldy, scales,
+                                                                     scale_ld, blocks, st, 0, dmask);
         case OS_TF32X2:
-            return launch_gather_t<float, Tf32Pair, kGatherQT, 1>(p, X, kStrip, ldx, F, wts, Yt, ldy, nullptr, scale_ld, blocks,
-                                                           st, plane_rows * ldy, dmask);
+            return launch_gather_t<float, Tf32Pair, kGatherQT, 1, kMis>(p, X, ss, ldx, F, wts, Yt, ldy, nullptr,
+                                                                       scale_ld, blocks, st, plane_rows * ldy, dmask);
     }
     return OS_ERR_DTYPE;
 }
@@ -852,19 +914,32 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
             return launch_quantize_fp8(p, stg, z, l, block_mask, BtT, ldbt, scales, fp8_scale_ld(l), st);
         }
     }
-    // FP32 input with 16-byte aligned rows: gather whole 128-wide strips in place,
-    // and pack only a ragged remainder of fewer than 128 columns.
-    const bool direct = b_t == OS_F32 && aligned16(B) && ldb % 4 == 0 && ldb * 4 < (int64_t(1) << 32) &&
-                        l >= kStrip;
+    // FP32 input: gather whole strips in place, and pack only a ragged remainder
+    // narrower than a strip.  Strips are 128 wide for 16-byte aligned rows; other
+    // rows are gathered in 124-wide strips (about twice the instructions per row
+    // piece: on GB300 that beats packing B first while at most 6 blocks are
+    // gathered, 1.82 vs 2.35 ms for 4 blocks of 65536 x 16383, and loses above,
+    // 3.28 vs 3.01 ms for 8 blocks).
+    const bool aligned = aligned16(B) && ldb % 4 == 0;
+    const uint64_t listed = (block_mask ? block_mask : ~0ull) & (p->P >= 64 ? ~0ull : (1ull << p->P) - 1);
+    const bool mis_pays = __builtin_popcountll(listed) <= 6;
+    const int64_t sw = aligned ? kStrip : kStrip - 4;
+    // (a misaligned strip reads up to 4 elements past its end: keep them in the row)
+    const int64_t lf = aligned ? l / sw * sw : (l >= 4 ? (l - 4) / sw * sw : 0);
+    const bool direct = b_t == OS_F32 && (reinterpret_cast<uintptr_t>(B) & 3u) == 0 &&
+                        ldb * 4 < (int64_t(1) << 32) && lf > 0 && (aligned || mis_pays);
     if (direct) {
-        const int64_t lf = l / kStrip * kStrip;
         // the workspace holds the remainder's strips (if any) and the entry weights
         if ((lf < l || row_scale) && (!ws || ws_bytes < sketch_workspace_bytes(p, l - lf, b_t)))
             return OS_ERR_WORKSPACE;
         const float *wts = nullptr;
         if (row_scale) OSK_TRY(make_weights(p, row_scale, block_mask, ws_weights(p, ws, l - lf, b_t), &wts, st));
-        OSK_TRY(launch_gather_direct(p, (const float *)B, ldb, lf, wts, BtT, out_t, ldbt, scales,
-                                     fp8_scale_ld(l), block_mask, st, l, dmask));
+        if (aligned)
+            OSK_TRY(launch_gather_direct<false>(p, (const float *)B, ldb, lf, wts, BtT, out_t, ldbt, scales,
+                                                fp8_scale_ld(l), block_mask, st, l, dmask));
+        else
+            OSK_TRY(launch_gather_direct<true>(p, (const float *)B, ldb, lf, wts, BtT, out_t, ldbt, scales,
+                                               fp8_scale_ld(l), block_mask, st, l, dmask));
         if (lf == l) return OS_OK;
         float *Xs = (float *)ws_base(ws);
         OSK_TRY(launch_pack_rows<float>((const float *)B + lf, ldb, p->n, l - lf, Xs, st));

@@ -86,7 +86,7 @@ SKETCH_CASES = [
     (32, 2048, 384, 256, 2, 1),        # right sketch: whole 128-wide strips only
     (130, 100_000, 70, 512, 3, 1),     # 4 windows of the sketched dimension, the last one ragged
     (64, 70_001, 200, 4096, 2, 1),     # 3 windows with few members per (window, bucket) list
-    (64, 20_000, 1023, 512, 3, 1),     # right operand rows not 16-byte aligned: 4-byte loads in place
+    (64, 20_000, 1023, 512, 3, 1),     # right operand rows not 16-byte aligned: 124-wide strips in place
 ]
 
 
@@ -175,6 +175,54 @@ def test_sketch_right_row_scale(ops, l, in_dtype):
     assert_fp32_within(BtT.cpu().numpy(), ref, bd)
     Bb, _ = ops.sketch_right(p, Bd, "bf16", row_scale=_dev(rs))
     assert_bf16_within(Bb.float().cpu().numpy(), ref, bd)
+
+
+@pytest.mark.parametrize("n,l,ldb,off,b,out,mask,N,e", [
+    (3000, 1023, 1023, 0, 256, "f32", 0, 3, 1),        # rows 4 bytes apart mod 16: all four classes
+    (5000, 500, 502, 0, 512, "f32", 0, 3, 1),          # two classes (row pitch 2 mod 4 elements)
+    (4096, 376, 377, 1, 256, "bf16", 0b1011, 3, 1),    # three 124-wide strips + 4 packed columns, base 4 B past 16
+    (2000, 128, 129, 3, 128, "f32", 0, 3, 1),          # one strip, base 12 bytes past 16
+    (2000, 127, 127, 0, 128, "f32", 0, 3, 1),          # a strip would read past the row: packed
+    (3000, 250, 251, 2, 256, "tf32x2", 0, 3, 1),       # two strips and a 2-column remainder, hi/lo planes
+    (3000, 260, 261, 0, 256, "fp8", 0b1101, 3, 1),     # FP8 epilogue in clusters of four
+    (3000, 1023, 1023, 0, 128, "f32", 0, 6, 2),        # 8 blocks gathered: packed instead
+    (3000, 1023, 1023, 0, 128, "bf16", 0b00111111, 6, 2),   # 6 of 8 blocks: in place again
+])
+def test_sketch_right_misaligned_rows(ops, n, l, ldb, off, b, out, mask, N, e):
+    # B rows that do not start on 16-byte boundaries are gathered in place (or
+    # packed when more than 6 blocks are gathered): each lane reads the 16-byte
+    # granule holding its first element and the sums are kept per misalignment
+    # class, so every kept element stays within the FP32 bound of the oracle's
+    # sketch and reruns are bitwise equal
+    rng = np.random.default_rng(n + l + off)
+    store = torch.from_numpy(rng.standard_normal((n + 1) * ldb).astype(np.float32)).cuda()
+    Bd = torch.as_strided(store, (n, l), (ldb, 1), off)     # row pitch ldb, first element off floats in
+    B64 = Bd.cpu().numpy().astype(np.float64)
+    p = ops.plan(n, b, N, e, 4)
+    h, s = oracle.hash_tables(n, b, N, e, 4)
+    ref, bd = sketch_bounds_right(B64, h, s, b)
+    ref, bd = ref.T, bd.T
+    keep = mask or (1 << (N + e)) - 1
+    cols = oracle.selected_columns(keep, N + e, b)
+    Y, sc = ops.sketch_right(p, Bd, out, block_mask=mask)
+    if out == "tf32x2":
+        hi, lo = ops.tf32_planes(Y)
+        got = hi.cpu().numpy().astype(np.float64) + lo.cpu().numpy().astype(np.float64)
+        assert_fp32_within(got[:, cols], ref[:, cols], bd[:, cols])
+    elif out == "bf16":
+        assert_bf16_within(Y.float().cpu().numpy()[:, cols], ref[:, cols], bd[:, cols])
+    elif out == "fp8":
+        scale_rows = ops.fp8_scales_by_row(sc, l).cpu().numpy()
+        slices = cols.reshape(-1, 128)[:, 0] // 128
+        assert_fp8_within(Y.float().cpu().numpy()[:, cols], scale_rows[:, slices], ref[:, cols], bd[:, cols])
+    else:
+        assert_fp32_within(Y.cpu().numpy()[:, cols], ref[:, cols], bd[:, cols])
+    Y2, _ = ops.sketch_right(p, Bd, out, block_mask=mask)
+    ct = torch.from_numpy(cols).cuda()
+    if out == "fp8":
+        assert torch.equal(Y.view(torch.uint8)[:, ct], Y2.view(torch.uint8)[:, ct])
+    else:
+        assert torch.equal(Y[:, ct], Y2[:, ct])
 
 
 @pytest.mark.parametrize("m,n,l,b,N,e", [(512, 4096, 512, 256, 4, 1), (200, 3000, 70, 128, 2, 1)])
