@@ -768,7 +768,7 @@ def run_hessian(args):
     else:
         # A is 1% dense: route only its nonzeros (Sec. 4's O(nnz) sketch), one CTA per row
         At, _ = ops.sketch_left_sparse(p, A, "bf16", col_scale=cs, block_mask=w.mask)
-        sk_name, sk_kernel = "sketch_left_sparse (col_scale)", "sketch_left_sparse_kernel"
+        sk_name, sk_kernel = "sketch_left_sparse (col_scale)", "sketch_left_onepass_kernel + sketch_left_sparse_kernel"
 
         def sketch():
             ops.sketch_left_sparse(p, A, "bf16", col_scale=cs, out=At, block_mask=w.mask)
@@ -811,7 +811,7 @@ def run_hessian(args):
            "input_dtype": "f32", "l2": "inputs (17.2 GB) larger than L2; no flush needed",
            "sketch": "dense gather" if args.dense_sketch else "sparse rows", "parallelism": f"replicas{world}"}
     line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, cpu,
-                 None, (4 if args.dense_sketch else 2) * args.steps, clk, err, world, gemm=gemm)
+                 None, (4 if args.dense_sketch else 3) * args.steps, clk, err, world, gemm=gemm)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -57,6 +57,39 @@ def test_sparse_sketch_fp32_parity(ops, m, n, b, N, e, density):
     assert torch.equal(At, At2)
 
 
+@pytest.mark.parametrize("out", ["f32", "bf16", "fp8"])
+def test_sparse_sketch_mixed_rows(ops, out):
+    # rows whose nonzeros fit the one-pass regions beside rows that overflow them
+    # (dense rows, and a row dense in one 32nd only) in one launch: every row
+    # within the oracle's bound, reruns bitwise equal
+    m, n, b, N, e = 24, 100_000, 1024, 5, 1
+    rng = np.random.default_rng(77)
+    A = _sparse(rng, m, n, 0.01, scale_rows=True)
+    A[3] = rng.standard_normal(n)                          # dense
+    A[10, 40_000:43_000] = rng.standard_normal(3000)       # one segment dense
+    A[17] = 0.0                                            # empty
+    A[18, ::5] = rng.standard_normal(len(range(0, n, 5)))  # 20 %: overflows, several flushes
+    A = A.astype(np.float32)
+    p = ops.plan(n, b, N, e, 6)
+    h, s = oracle.hash_tables(n, b, N, e, 6)
+    mask = 0b101111
+    Y, sc = ops.sketch_left_sparse(p, _dev(A), out, block_mask=mask)
+    ref, bd = sketch_bounds_left(A, h, s, b)
+    cols = oracle.selected_columns(mask, N + e, b)
+    if out == "fp8":
+        scale_rows = ops.fp8_scales_by_row(sc, m).cpu().numpy()
+        slices = cols.reshape(-1, 128)[:, 0] // 128
+        assert_fp8_within(Y.float().cpu().numpy()[:, cols], scale_rows[:, slices], ref[:, cols], bd[:, cols])
+    elif out == "bf16":
+        assert_bf16_within(Y.float().cpu().numpy()[:, cols], ref[:, cols], bd[:, cols])
+    else:
+        assert_fp32_within(Y.cpu().numpy()[:, cols], ref[:, cols], bd[:, cols])
+    Y2, _ = ops.sketch_left_sparse(p, _dev(A), out, block_mask=mask)
+    ct = torch.from_numpy(cols).cuda()
+    assert torch.equal(Y.view(torch.uint8)[:, ct] if out == "fp8" else Y[:, ct],
+                       Y2.view(torch.uint8)[:, ct] if out == "fp8" else Y2[:, ct])
+
+
 def test_sparse_sketch_special_rows(ops):
     # all-zero rows, one nonzero at the last index, one at index 0, n = 1
     n, b, N, e = 33_333, 128, 2, 1
