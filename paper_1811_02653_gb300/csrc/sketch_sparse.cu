@@ -661,20 +661,36 @@ sketch_left_onepass_kernel(const InT *__restrict__ A, int64_t lda, int64_t m, in
     }
 }
 
-// The flushing kernel: one CTA per row (persistent over rows); with
-// marked_only, only the rows the one-pass kernel marked.
-template <typename InT, typename OutT, bool kScale>
+// The flushing kernel: one CTA per row (persistent over rows); with kMarked,
+// only the rows the one-pass kernel marked.
+template <typename InT, typename OutT, bool kScale, bool kMarked>
 __global__ void __launch_bounds__(kSpThreads, 1)
 sketch_left_sparse_kernel(const InT *__restrict__ A, int64_t lda, int64_t m, int64_t n, bool vec,
                           const uint32_t *__restrict__ hs, uint64_t seed, bool hashed, int32_t b,
-                          BlockList blocks, int emax, bool marked_only,
+                          BlockList blocks, int emax,
                           const float *__restrict__ col_scale, OutT *__restrict__ At, int64_t ldat,
                           float *__restrict__ scales, int64_t lds, int64_t plane_elems) {
     extern __shared__ float4 sp_smem[];
-    for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
-        if (marked_only && *row_mark(At, r, ldat, (int64_t)blocks.idx[0] * b) != RowMark<OutT>::bits) continue;
-        sp_row_flushing<InT, OutT, kScale>(A + r * lda, r, n, vec, hs, seed, hashed, b, blocks, emax, col_scale,
-                                           At, ldat, scales, lds, plane_elems, sp_smem);
+    if constexpr (kMarked) {
+        // 32 of the CTA's rows at a time: every warp reads their marks (the same
+        // ballot in every warp), then the CTA runs the marked ones
+        const int lane = threadIdx.x & 31;
+        for (int64_t base = blockIdx.x; base < m; base += (int64_t)gridDim.x * 32) {
+            const int64_t rl = base + (int64_t)lane * gridDim.x;
+            const bool take = rl < m && *row_mark(At, rl, ldat, (int64_t)blocks.idx[0] * b) == RowMark<OutT>::bits;
+            uint32_t todo = __ballot_sync(0xffffffffu, take);
+            while (todo) {
+                const int t = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t r = base + (int64_t)t * gridDim.x;
+                sp_row_flushing<InT, OutT, kScale>(A + r * lda, r, n, vec, hs, seed, hashed, b, blocks, emax,
+                                                   col_scale, At, ldat, scales, lds, plane_elems, sp_smem);
+            }
+        }
+    } else {
+        for (int64_t r = blockIdx.x; r < m; r += gridDim.x)
+            sp_row_flushing<InT, OutT, kScale>(A + r * lda, r, n, vec, hs, seed, hashed, b, blocks, emax,
+                                               col_scale, At, ldat, scales, lds, plane_elems, sp_smem);
     }
 }
 
@@ -725,11 +741,13 @@ os_status launch_sparse_t(const InT *A, int64_t lda, int64_t m, int64_t n, const
                                                       plane_elems);
         OSK_TRY(check_launch());
     }
-    auto k = col_scale ? sketch_left_sparse_kernel<InT, OutT, true> : sketch_left_sparse_kernel<InT, OutT, false>;
+    auto k = cw > 0 ? (col_scale ? sketch_left_sparse_kernel<InT, OutT, true, true>
+                                 : sketch_left_sparse_kernel<InT, OutT, false, true>)
+                    : (col_scale ? sketch_left_sparse_kernel<InT, OutT, true, false>
+                                 : sketch_left_sparse_kernel<InT, OutT, false, false>);
     OSK_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0));
     k<<<(unsigned)grid, kSpThreads, smem0, st>>>(A, lda, m, n, vec, p->hs, p->seed, p->hashed != 0, p->b, blocks,
-                                                 emax, cw > 0, col_scale, (OutT *)At, ldat, scales, lds,
-                                                 plane_elems);
+                                                 emax, col_scale, (OutT *)At, ldat, scales, lds, plane_elems);
     return check_launch();
 }
 
