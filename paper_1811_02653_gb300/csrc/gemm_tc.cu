@@ -123,7 +123,19 @@ struct GemmArgs {
     const uint64_t *block_masks;
     int64_t bm, bn;
     int32_t nbc, P;
+    // CTA-pair kernel, C = A A^T (B is A): only the tile pairs on and below the
+    // diagonal are computed; each off-diagonal one is also stored transposed
+    int32_t sym;
 };
+
+// Tile pair t of the lower triangle (row-major: pair row pm, tile column tn <= pm).
+__device__ __forceinline__ void tri_coords(int t, int &pm, int &tn) {
+    int r = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    pm = r;
+    tn = t - r * (r + 1) / 2;
+}
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
     // Groups of 16 m-tiles: consecutive tiles share A panels and nearby B panels.
@@ -618,7 +630,8 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
 
     auto coords = [&](int t, int &tm, int &tn) {
         int pm = 0;
-        tile_coords(t, tiles_mp, g.tiles_n, pm, tn);
+        if (g.sym) tri_coords(t, pm, tn);
+        else tile_coords(t, tiles_mp, g.tiles_n, pm, tn);
         tm = 2 * pm + rank;   // past the last tile (odd count): zero rows, no stores
     };
     // kept sketch blocks of the block of C holding tile pair (tm / 2, tn) (the pair's
@@ -779,6 +792,19 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
                             }
                         }
                     }
+                    if (g.sym && (tm >> 1) != tn) {
+                        // the mirror tile: value (r, cb + u) also at (cb + u, r); the
+                        // warp's 32 rows make each of these stores one 128-byte line
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) {
+                            if (cb + u < g.l) {
+                                float *dt = g.C + (cb + u) * g.ldc + r;
+                                float o = alpha * __uint_as_float(v[u]);
+                                if (g.beta != 0.f) o = fmaf(g.beta, *dt, o);
+                                *dt = o;
+                            }
+                        }
+                    }
                 }
             }
             tc_fence_before();
@@ -908,6 +934,8 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
 }
 
 // BF16 on CTA pairs (gemm_pair_bf16_kernel): 256 x 256 tiles, two SMs each.
+// C = A A^T (B the same matrix as A) is symmetric: only the lower triangle of
+// tile pairs is computed and mirrored.
 os_status launch_pair_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l, int64_t zK,
                            int32_t blk, const BlockList &kept, float alpha, float beta, float *Cout, int64_t ldc,
                            cudaStream_t st, const uint64_t *block_masks = nullptr, int64_t bm = 0,
@@ -927,6 +955,8 @@ os_status launch_pair_bf16(const void *A, int64_t lda, const void *B, int64_t ld
     g.tiles_m = (int)((m + BM - 1) / BM);
     g.tiles_n = (int)((l + C::BN - 1) / C::BN);
     g.num_tiles = (g.tiles_m + 1) / 2 * g.tiles_n;   // tile pairs
+    g.sym = A == B && lda == ldb && m == l && !block_masks;
+    if (g.sym) g.num_tiles = g.tiles_n * (g.tiles_n + 1) / 2;   // tiles_n = (tiles_m + 1) / 2
     g.alpha = alpha;
     g.beta = beta;
     g.C = Cout;

@@ -124,6 +124,36 @@ def test_symmetric_product(ops):
     assert oracle.rel_frob(H, H.T) <= 1e-6
 
 
+@pytest.mark.parametrize("m,b,N,e,mask,beta", [
+    (300, 128, 3, 2, 0b10101, 0.0),       # two tile pairs per side, the last pair half empty
+    (1000, 256, 4, 1, 0b11011, 0.0),      # 4 x 4 pairs: 10 computed, 6 mirrored
+    (4096, 512, 3, 1, 0b1011, 0.5),       # 16 x 16 pairs (more than the clusters), beta C added
+    (1, 64, 1, 0, 0b1, 0.0),              # a single element
+])
+def test_gemm_bf16_symmetric_lower_triangle(ops, m, b, N, e, mask, beta):
+    # At At^T with the same operand twice computes the tile pairs on and below the
+    # diagonal and stores each off-diagonal one transposed as well: the same bits
+    # as the general kernel in the lower triangle, an exactly symmetric C, and
+    # within the FP32 accumulation bound of the oracle everywhere
+    rng = np.random.default_rng(m + b)
+    z = (N + e) * b
+    At, At64 = _bf16(rng.standard_normal((m, z)))
+    p = ops.plan(max(z, 64), b, N, e, 0)
+    C0 = torch.from_numpy(rng.standard_normal((m, m)).astype(np.float32)).cuda()
+    C_sym = ops.gemm_masked(p, At, At, mask, beta=beta, C=C0.clone())
+    C_gen = ops.gemm_masked(p, At, At.clone(), mask, beta=beta, C=C0.clone())
+    low = torch.tril(torch.ones((m, m), dtype=torch.bool, device="cuda"))
+    pair = torch.arange(m, device="cuda") // 256
+    low |= pair[:, None] == pair[None, :]            # whole diagonal pairs come from the kernel
+    assert torch.equal(C_sym[low], C_gen[low])
+    assert torch.equal(C_sym, C_sym.T) or beta != 0.0
+    ref = oracle.masked_product(At64, At64.T, b, mask) + beta * C0.cpu().numpy().astype(np.float64)
+    K = bin(mask).count("1") * b
+    absref = oracle.masked_product(np.abs(At64), np.abs(At64).T, b, mask) + abs(beta) * np.abs(C0.cpu().numpy())
+    bound = 2 * (K + 1) * 2.0 ** -24 * absref + 1e-30
+    assert (np.abs(C_sym.cpu().numpy() - ref) <= bound).all()
+
+
 def _split_tf32(x):
     """hi = x with the low 13 mantissa bits cleared (exact in TF32), lo = x - hi."""
     x = np.ascontiguousarray(x, dtype=np.float32)
