@@ -491,19 +491,37 @@ __global__ void __launch_bounds__(256) unsketch_cols_kernel(
 // The same sums with the CTA's R rows of T staged in shared memory: a CTA owns
 // rows r0 .. r0+R-1 of dX and sweeps all n columns, so each table entry h_j(i)
 // is read once for R rows and the k random reads per output hit shared memory
-// instead of a 32-byte L2 sector each.  Same order of operations as above, so
-// the results are bitwise equal.
+// instead of a 32-byte L2 sector each.  The R rows are interleaved (column c of
+// the R rows at ts[c*R .. c*R+R-1]): one 4R-byte shared load serves all R
+// rows.  Same order of operations as above, so the results are bitwise equal.
+template <int R> struct RowVec;
+template <> struct RowVec<1> { using T = float; };
+template <> struct RowVec<2> { using T = float2; };
+template <> struct RowVec<4> { using T = float4; };
+template <int R>
+__device__ __forceinline__ float row_of(const typename RowVec<R>::T &v, int r) {
+    if constexpr (R == 1) return v;
+    else if constexpr (R == 2) return r == 0 ? v.x : v.y;
+    else return r == 0 ? v.x : r == 1 ? v.y : r == 2 ? v.z : v.w;
+}
+
 template <typename OutT, int R>
-__global__ void __launch_bounds__(256) unsketch_cols_smem_kernel(
+__global__ void __launch_bounds__(512) unsketch_cols_smem_kernel(
     const float *__restrict__ T, int64_t m, int64_t ldt, int64_t kb, const uint32_t *__restrict__ hs, int64_t n,
     int32_t b, BlockList kept, float scale, OutT *__restrict__ dX, int64_t ldx) {
+    using V = typename RowVec<R>::T;
     extern __shared__ float4 ts4[];
-    float *ts = reinterpret_cast<float *>(ts4);     // [R][kb]
+    V *ts = reinterpret_cast<V *>(ts4);     // [kb] columns of R interleaved rows
     const int64_t r0 = (int64_t)blockIdx.x * R;
     const int rows = (int)(m - r0 < R ? m - r0 : R);
-    for (int r = 0; r < rows; ++r) {
-        const float *src = T + (r0 + r) * ldt;
-        for (int64_t c = threadIdx.x; c < kb; c += blockDim.x) ts[r * kb + c] = __ldg(src + c);
+    for (int64_t c = threadIdx.x; c < kb; c += blockDim.x) {
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (r < rows) x[r] = __ldg(T + (r0 + r) * ldt + c);
+        if constexpr (R == 1) ts[c] = x[0];
+        else if constexpr (R == 2) ts[c] = make_float2(x[0], x[1]);
+        else ts[c] = make_float4(x[0], x[1], x[2], x[3]);
     }
     __syncthreads();
     // four columns per thread and pass, so that four table loads per kept block
@@ -515,22 +533,32 @@ __global__ void __launch_bounds__(256) unsketch_cols_smem_kernel(
         for (int u = 0; u < NI; ++u)
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[u][r] = 0.f;
-        for (int t = 0; t < kept.count; ++t) {
-            const uint32_t *hrow = hs + (int64_t)kept.idx[t] * n;
-            uint32_t v[NI];
+        // the table entries of four kept blocks at a time: 16 loads in flight
+        constexpr int TB = 4;
+        for (int t0 = 0; t0 < kept.count; t0 += TB) {
+            uint32_t v[TB][NI];
 #pragma unroll
-            for (int u = 0; u < NI; ++u) {
-                const int64_t i = i0 + (int64_t)u * blockDim.x;
-                v[u] = i < n ? __ldg(hrow + i) : 0u;
+            for (int tt = 0; tt < TB; ++tt) {
+                const uint32_t *hrow = hs + (int64_t)kept.idx[t0 + tt < kept.count ? t0 + tt : t0] * n;
+#pragma unroll
+                for (int u = 0; u < NI; ++u) {
+                    const int64_t i = i0 + (int64_t)u * blockDim.x;
+                    v[tt][u] = i < n && t0 + tt < kept.count ? __ldg(hrow + i) : 0u;
+                }
             }
 #pragma unroll
-            for (int u = 0; u < NI; ++u) {
-                const int64_t c = (int64_t)t * b + (v[u] & kIndexMask);   // kept blocks compacted
-                const bool neg = (v[u] & kSignBit) != 0u;
+            for (int tt = 0; tt < TB; ++tt) {
+                if (t0 + tt >= kept.count) break;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float x = ts[r * kb + c];
-                    acc[u][r] += neg ? -x : x;
+                for (int u = 0; u < NI; ++u) {
+                    const int64_t c = (int64_t)(t0 + tt) * b + (v[tt][u] & kIndexMask);   // kept blocks compacted
+                    const bool neg = (v[tt][u] & kSignBit) != 0u;
+                    const V xv = ts[c];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float x = row_of<R>(xv, r);
+                        acc[u][r] += neg ? -x : x;
+                    }
                 }
             }
         }
@@ -552,10 +580,6 @@ __global__ void __launch_bounds__(256) unsketch_cols_smem_kernel(
     }
 }
 
-// dG[i, c] = scale * sum_{t < k} sigma_j(i) U[t*b + h_j(i), c], j = kept[t] (U holds
-// the kept blocks only); one warp per row i and 1024 columns: for each kept block
-// the warp reads the bucket's row of U with 32 independent loads per lane, and
-// the 32 sums per lane stay in registers.
 template <typename OutT>
 __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     const float *__restrict__ U, int64_t l, int64_t ldu, const uint32_t *__restrict__ hs, int64_t n,
@@ -971,18 +995,18 @@ os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t l
     if (m == 0) return OS_OK;   // an empty dX
     if (!T || !dX) return OS_ERR_INVALID_ARG;
     const BlockList kept = mask_to_list(mask, p->P);
-    // rows of T staged per CTA: the most that keep two or more CTAs per SM (up to
-    // 96 KB each), else one row in up to 200 KB, else the unstaged kernel
+    // rows of T staged per CTA (512 threads): 4, 2 or 1, the most that fit in
+    // 200 KB, else the unstaged kernel
     const int64_t kb = (int64_t)kcnt * p->b;
     const size_t row_bytes = (size_t)kb * sizeof(float);
-    const int R = row_bytes * 4 <= 96 * 1024 ? 4 : row_bytes * 2 <= 96 * 1024 ? 2 : row_bytes <= 200 * 1024 ? 1 : 0;
+    const int R = row_bytes * 4 <= 200 * 1024 ? 4 : row_bytes * 2 <= 200 * 1024 ? 2 : row_bytes <= 200 * 1024 ? 1 : 0;
     if (R > 0) {
         const size_t smem = row_bytes * R;
         const unsigned gxs = (unsigned)((m + R - 1) / R);
         auto launch = [&](auto kern, auto *out) -> os_status {
             if (smem > 48 * 1024)
                 OSK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<gxs, 256, smem, st>>>(T, m, ldt, kb, p->hs, p->n, p->b, kept, scale, out, ldx);
+            kern<<<gxs, 512, smem, st>>>(T, m, ldt, kb, p->hs, p->n, p->b, kept, scale, out, ldx);
             return check_launch();
         };
         if (x_t == OS_F32) {
