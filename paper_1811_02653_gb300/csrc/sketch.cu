@@ -616,6 +616,54 @@ __global__ void __launch_bounds__(256) unsketch_rows_kernel(
     }
 }
 
+// The same sums with 16-byte accesses (l, ldu and ldg multiples of 4, U and dG
+// 16-byte aligned): lane t covers columns 4t .. 4t+3 of every 128-column group,
+// a quarter of the load instructions for the same bytes.  Same order of
+// operations, so the results are bitwise equal.
+template <typename OutT>
+__global__ void __launch_bounds__(256) unsketch_rows_vec_kernel(
+    const float *__restrict__ U, int64_t l, int64_t ldu, const uint32_t *__restrict__ hs, int64_t n,
+    int32_t b, BlockList kept, float scale, OutT *__restrict__ dG, int64_t ldg) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    if (i >= n) return;
+    const int64_t c0 = (int64_t)blockIdx.y * 1024 + 4 * lane;
+    float4 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t v_lo = lane < kept.count ? __ldg(hs + (int64_t)kept.idx[lane] * n + i) : 0u;
+    const uint32_t v_hi = lane + 32 < kept.count ? __ldg(hs + (int64_t)kept.idx[lane + 32] * n + i) : 0u;
+    for (int t = 0; t < kept.count; ++t) {
+        const uint32_t v = __shfl_sync(0xffffffffu, t < 32 ? v_lo : v_hi, t & 31);
+        const float sg = (v & kSignBit) ? -scale : scale;
+        const float *urow = U + ((int64_t)t * b + (v & kIndexMask)) * ldu;   // kept blocks compacted
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t c = c0 + 128 * q;
+            if (c < l) {
+                const float4 u = __ldg(reinterpret_cast<const float4 *>(urow + c));
+                acc[q].x = fmaf(sg, u.x, acc[q].x);
+                acc[q].y = fmaf(sg, u.y, acc[q].y);
+                acc[q].z = fmaf(sg, u.z, acc[q].z);
+                acc[q].w = fmaf(sg, u.w, acc[q].w);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int64_t c = c0 + 128 * q;
+        if (c < l) {
+            if constexpr (sizeof(OutT) == 4) {
+                *reinterpret_cast<float4 *>(dG + i * ldg + c) = acc[q];
+            } else {
+                __nv_bfloat162 h[2] = {__floats2bfloat162_rn(acc[q].x, acc[q].y),
+                                       __floats2bfloat162_rn(acc[q].z, acc[q].w)};
+                *reinterpret_cast<uint2 *>(dG + i * ldg + c) = *reinterpret_cast<uint2 *>(h);
+            }
+        }
+    }
+}
+
 // The signed scale of every entry of the listed blocks' padded bucket lists,
 // in list order: w[j][pos] = sigma_j(i) * s_i for the entry (i, sigma) at pos
 // (0 for padding), so the gather loads the weights of 32 entries with one
@@ -1043,12 +1091,22 @@ os_status unsketch_rows_impl(const Plan *p, const float *U, int64_t l, int64_t l
     const BlockList kept = mask_to_list(mask, p->P);
     dim3 grid((unsigned)((p->n + 7) / 8), (unsigned)((l + 1023) / 1024));
     if (grid.y > 65535u) return OS_ERR_UNSUPPORTED;
-    if (g_t == OS_F32)
-        unsketch_rows_kernel<float><<<grid, 256, 0, st>>>(U, l, ldu, p->hs, p->n, p->b, kept, scale,
-                                                          (float *)dG, ldg);
-    else
-        unsketch_rows_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(U, l, ldu, p->hs, p->n, p->b, kept,
-                                                                  scale, (__nv_bfloat16 *)dG, ldg);
+    const bool vec = l % 4 == 0 && ldu % 4 == 0 && ldg % 4 == 0 && aligned16(U) && aligned16(dG);
+    if (g_t == OS_F32) {
+        if (vec)
+            unsketch_rows_vec_kernel<float><<<grid, 256, 0, st>>>(U, l, ldu, p->hs, p->n, p->b, kept, scale,
+                                                                  (float *)dG, ldg);
+        else
+            unsketch_rows_kernel<float><<<grid, 256, 0, st>>>(U, l, ldu, p->hs, p->n, p->b, kept, scale,
+                                                              (float *)dG, ldg);
+    } else {
+        if (vec)
+            unsketch_rows_vec_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(U, l, ldu, p->hs, p->n, p->b, kept,
+                                                                          scale, (__nv_bfloat16 *)dG, ldg);
+        else
+            unsketch_rows_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(U, l, ldu, p->hs, p->n, p->b, kept,
+                                                                      scale, (__nv_bfloat16 *)dG, ldg);
+    }
     return check_launch();
 }
 

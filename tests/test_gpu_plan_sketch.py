@@ -321,8 +321,9 @@ def test_sketch_argument_errors(ops):
         ops.sketch_left(p, A, "f32", workspace=ws)                         # workspace too small
 
 
-def test_unsketch_parity(ops):
-    m, n, l, b, N, e = 64, 3000, 96, 128, 4, 1
+@pytest.mark.parametrize("l", [96, 99, 2100])   # 16-byte rows of U and dG (vector kernel), odd, several 1024-column slabs
+def test_unsketch_parity(ops, l):
+    m, n, b, N, e = 64, 3000, 128, 4, 1
     mask = 0b10111
     rng = np.random.default_rng(14)
     z = (N + e) * b
@@ -351,7 +352,8 @@ def test_unsketch_parity(ops):
 
 @pytest.mark.parametrize("m,n,b,N,e,mask,out", [
     (66, 3000, 128, 4, 1, 0b10111, "f32"),      # rows of T staged 4 per CTA, last CTA partial
-    (5, 20_000, 2048, 4, 1, 0b11011, "bf16"),   # 2 per CTA (the autograd workload's k b = 8192)
+    (5, 20_000, 2048, 4, 1, 0b11011, "bf16"),   # 4 per CTA (the autograd workload's k b = 8192), last CTA 1
+    (7, 6000, 4096, 4, 1, 0b10111, "bf16"),     # 2 per CTA (64 KB rows), last CTA 1
     (3, 9000, 8192, 4, 1, 0b01111, "f32"),      # one 128 KB row per CTA
     (2, 5000, 16384, 4, 0, 0b1111, "f32"),      # rows too long to stage: the unstaged kernel
 ])
