@@ -780,13 +780,15 @@ os_status launch_gather_t(const Plan *p, const InT *X, int64_t strip_stride, int
 // gathered rows hit L2 (right sketch 1.89 -> 1.74 ms on GB300).
 constexpr int kGatherQT = 16;
 
+// ss, W: the distance between strips and between rows of a strip (elements);
+// the defaults are the packed workspace layout.
 template <typename InT>
 os_status launch_gather(const Plan *p, const InT *Xs, int64_t F, const float *wts, void *Yt,
                         os_dtype out_t, int64_t ldy, float *scales, int64_t scale_ld, uint64_t block_mask,
-                        cudaStream_t st, int64_t plane_rows = 0, const uint64_t *dmask = nullptr) {
+                        cudaStream_t st, int64_t plane_rows = 0, const uint64_t *dmask = nullptr,
+                        int64_t ss = -1, int64_t W = strip_of<InT>()) {
     const BlockList blocks = mask_to_list(block_mask ? block_mask : ~0ull, p->P);
-    constexpr int64_t W = strip_of<InT>();
-    const int64_t ss = p->n * W;
+    if (ss < 0) ss = p->n * W;
     switch (out_t) {
         case OS_F32:
             return launch_gather_t<InT, float, kGatherQT, 1>(p, Xs, ss, W, F, wts, Yt, ldy, scales, scale_ld, blocks, st, 0, dmask);
@@ -1018,6 +1020,26 @@ os_status sketch_right_impl(const Plan *p, const void *B, os_dtype b_t, int64_t 
         char *yt = (char *)BtT + (size_t)lf * ldbt * dtype_size(out_t);
         float *sc = scales ? scales + lf : nullptr;   // slice-major: the remainder's rows start at lf
         return launch_gather<float>(p, Xs, l - lf, wts, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask, st, l, dmask);
+    }
+    // BF16 input with 16-byte aligned rows: 256-wide strips gathered in place (the
+    // same 512-byte row pieces as a packed strip), a ragged remainder packed
+    constexpr int64_t sw16 = strip_of<__nv_bfloat16>();
+    const int64_t lf16 = l / sw16 * sw16;
+    if (b_t == OS_BF16 && aligned16(B) && ldb % 8 == 0 && ldb * 2 < (int64_t(1) << 32) && lf16 > 0) {
+        if ((lf16 < l || row_scale) && (!ws || ws_bytes < sketch_workspace_bytes(p, l - lf16, b_t)))
+            return OS_ERR_WORKSPACE;
+        const float *wts = nullptr;
+        if (row_scale) OSK_TRY(make_weights(p, row_scale, block_mask, ws_weights(p, ws, l - lf16, b_t), &wts, st));
+        const __nv_bfloat16 *Bh = (const __nv_bfloat16 *)B;
+        OSK_TRY(launch_gather<__nv_bfloat16>(p, Bh, lf16, wts, BtT, out_t, ldbt, scales, fp8_scale_ld(l), block_mask,
+                                             st, l, dmask, sw16, ldb));
+        if (lf16 == l) return OS_OK;
+        __nv_bfloat16 *Xs = (__nv_bfloat16 *)ws_base(ws);
+        OSK_TRY(launch_pack_rows<__nv_bfloat16>(Bh + lf16, ldb, p->n, l - lf16, Xs, st));
+        char *yt = (char *)BtT + (size_t)lf16 * ldbt * dtype_size(out_t);
+        float *sc = scales ? scales + lf16 : nullptr;
+        return launch_gather<__nv_bfloat16>(p, Xs, l - lf16, wts, yt, out_t, ldbt, sc, fp8_scale_ld(l), block_mask,
+                                            st, l, dmask);
     }
     if (!ws || ws_bytes < sketch_workspace_bytes(p, l, b_t)) return OS_ERR_WORKSPACE;
     void *Xs = ws_base(ws);

@@ -225,6 +225,35 @@ def test_sketch_right_misaligned_rows(ops, n, l, ldb, off, b, out, mask, N, e):
         assert torch.equal(Y[:, ct], Y2[:, ct])
 
 
+@pytest.mark.parametrize("l,ldb,out,scaled", [
+    (512, 512, "f32", False),      # two 256-wide BF16 strips in place
+    (600, 600, "bf16", True),      # two strips in place + an 88-column packed remainder, row scale
+    (300, 304, "fp8", False),      # one strip + 44 packed columns, padded rows
+    (520, 521, "f32", False),      # rows not 16-byte aligned: packed
+])
+def test_sketch_right_bf16_in_place(ops, l, ldb, out, scaled):
+    # a BF16 right operand with 16-byte aligned rows is gathered in place in
+    # 256-wide strips (512-byte row pieces, as from a packed strip)
+    n, b, N, e = 5000, 256, 3, 1
+    rng = np.random.default_rng(l + ldb)
+    store = torch.from_numpy(rng.standard_normal((n, ldb)).astype(np.float32)).to(torch.bfloat16).cuda()
+    Bd = store[:, :l]
+    B64 = Bd.float().cpu().numpy().astype(np.float64)
+    rs = np.sqrt(10.0 ** rng.uniform(-3, 3, n)).astype(np.float32) if scaled else None
+    p = ops.plan(n, b, N, e, 8)
+    h, s = oracle.hash_tables(n, b, N, e, 8)
+    Y, sc = ops.sketch_right(p, Bd, out, row_scale=_dev(rs) if scaled else None)
+    ref, bd = sketch_bounds_left(np.ascontiguousarray(B64.T), h, s, b, rs)
+    if out == "fp8":
+        assert_fp8_within(Y.float().cpu().numpy(), ops.fp8_scales_by_row(sc, l).cpu().numpy(), ref, bd)
+    elif out == "bf16":
+        assert_bf16_within(Y.float().cpu().numpy(), ref, bd)
+    else:
+        assert_fp32_within(Y.cpu().numpy(), ref, bd)
+    Y2, _ = ops.sketch_right(p, Bd, out, row_scale=_dev(rs) if scaled else None)
+    assert torch.equal(Y.view(torch.uint8), Y2.view(torch.uint8))
+
+
 @pytest.mark.parametrize("m,n,l,b,N,e", [(512, 4096, 512, 256, 4, 1), (200, 3000, 70, 128, 2, 1)])
 def test_sketch_bf16_parity(ops, m, n, l, b, N, e):
     rng = np.random.default_rng(11)
