@@ -14,8 +14,8 @@
 //   1. compaction: warp w streams the w-th 32nd of the row (16 elements per
 //      lane per step, the next step's loads issued before this one is
 //      processed, an L2 prefetch two steps ahead) and appends its nonzeros
-//      (index, value) to its own region in ascending index order: warp
-//      ballots and scans only, no block barrier;
+//      (index, value) to its own region in ascending index order: warp scans
+//      only, no block barrier;
 //   2. per kept block: bucket codes h_j(i), sigma_j(i) of every entry and the
 //      bucket counts (integer shared-memory atomics), a scan into bucket
 //      starts, a scatter of entry numbers into their buckets, then each thread
@@ -431,10 +431,11 @@ __device__ __forceinline__ Sp1Smem sp1_layout(void *base, int b, int cw) {
 }
 
 // The row in one pass (b <= 4096, at most cw nonzeros in each 32nd of the row):
-//   1. warp w compacts the w-th 32nd of the row into its own region (warp
-//      ballots, no block barrier), entries in ascending index order; an L2
-//      prefetch runs 8 loads ahead, and the start of the next row is
-//      prefetched before the routing;
+//   1. warp w compacts the w-th 32nd of the row into its own region (a warp
+//      scan of each lane's nonzero count, no block barrier), entries in
+//      ascending index order; each step's loads are issued before the previous
+//      step is processed, an L2 prefetch runs two steps ahead, and the start of
+//      the next row is prefetched before the routing;
 //   2. per kept block: codes and bucket counts (integer atomics), a scan into
 //      bucket starts, a scatter of entry numbers into their buckets, then each
 //      thread sums the members of its 4 buckets in ascending entry order (the
