@@ -45,6 +45,29 @@ def test_host_matches_device(ops, m, n, l, b, N, e, dtype):
         assert oracle.rel_frob(C_h.numpy(), oracle.oversketch(A, B, h, s, b, mask)) <= 1e-5
 
 
+@pytest.mark.parametrize("l", [777, 512])
+def test_host_bf16_operands_match_device(ops, l):
+    # BF16 operands: B's device copy gets 16-byte rows and is gathered in place,
+    # the device entry point on B.cuda() packs it when l is not a multiple of 8;
+    # the sums are the same in the same order, so C is bitwise equal
+    m, n, b, N, e = 600, 8192, 256, 4, 1
+    rng = np.random.default_rng(l)
+    A = torch.from_numpy(rng.standard_normal((m, n)).astype(np.float32)).to(torch.bfloat16)
+    B = torch.from_numpy(rng.standard_normal((n, l)).astype(np.float32)).to(torch.bfloat16)
+    p = ops.plan(n, b, N, e, 3)
+    mask = 0b11101
+    C_h = ops.matmul_host(p, A.pin_memory(), B.pin_memory(), mask, "bf16")
+    torch.cuda.synchronize()
+    C_d = ops.matmul(p, A.cuda(), B.cuda(), mask, "bf16").cpu()
+    assert torch.equal(C_h, C_d)
+    h, s = oracle.hash_tables(n, b, N, e, 3)
+    A64 = A.float().numpy().astype(np.float64)
+    B64 = B.float().numpy().astype(np.float64)
+    ref = oracle.masked_product(oracle.round_bf16(oracle.sketch_left(A64, h, s, b)),
+                                oracle.round_bf16(oracle.sketch_right(B64, h, s, b)), b, mask)
+    assert oracle.rel_frob(C_h.numpy(), ref) <= 1e-4
+
+
 def test_host_symmetric_sparse_unpinned_and_strided(ops):
     m, n, b, N, e = 700, 20_000, 512, 6, 1
     rng = np.random.default_rng(3)
