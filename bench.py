@@ -963,9 +963,9 @@ def run_autograd(args):
            "metric_note": "effective flop = 6mnl (forward + dX + dG as exact GEMMs)",
            "l2": "inputs (1.07 GB) larger than L2; no flush needed", "parallelism": f"replicas{world}"}
     # per step: forward pack + gather of X, the in-place gather of G and the masked GEMM
-    # (4); backward cast, three layout transposes, two GEMMs and two unsketch kernels
-    # (8), plus the two sketches again (3) with --recompute
-    launches = (12 + (3 if args.recompute else 0)) * args.steps
+    # (4); backward: dC cast to BF16, two GEMMs reading the sketches and dC MN-major,
+    # two unsketch kernels (5); plus the two sketches again (3) with --recompute
+    launches = (9 + (3 if args.recompute else 0)) * args.steps
     line = _line(args, w.name, value, ms, "bf16", cfg, per, roof, cpu, None, launches, clk, err, world)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -27,6 +27,9 @@ os_status sketch_left_sparse_impl(const Plan *p, const void *A, os_dtype a_t, in
 os_status gemm_masked_f32(const Plan *p, const float *At, int64_t ldat, const float *BtT,
                           int64_t ldbt, int64_t m, int64_t l, uint64_t mask, float alpha, float beta,
                           float *C, int64_t ldc, cudaStream_t st);
+os_status gemm_bf16_mn(const void *A, int64_t lda, bool a_mn, const void *B, int64_t ldb, bool b_mn, int64_t m,
+                       int64_t l, int64_t K, float alpha, float *C, int64_t ldc, int32_t mn_b, int32_t remap,
+                       uint64_t mask, int32_t P, cudaStream_t st);
 os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const float *a_scales,
                          const void *BtT, int64_t ldbt, const float *b_scales, os_dtype dt, int64_t m,
                          int64_t l, uint64_t mask, float alpha, float beta, float *C, int64_t ldc,
@@ -478,28 +481,34 @@ extern "C" os_status oversketch_matmul_host(oversketch_plan_t plan, const void *
 namespace osk {
 namespace {
 
+// Workspace of the backward pass: dC in BF16 (both products use it), then T (and
+// the compacted kept blocks of B~, laid out K-major) for dX, then U (and A~'s kept
+// blocks and dC^T, K-major) for dG.  With b a multiple of 64 the tensor cores read
+// B~^T, A~ and dC MN-major as they are stored, and the K-major copies are not made.
 struct BackwardLayout {
+    bool mn;                         // operands read MN-major (no transposed copies)
     int64_t kb, ld_l, ld_m, ld_kb;   // padded row pitches (elements) of the BF16 / FP32 buffers
     size_t dc16, bsel, t, asel, dct16, u;
 };
 
 BackwardLayout backward_layout(const Plan *p, int64_t m, int64_t l, uint64_t mask) {
     BackwardLayout L;
+    L.mn = p->b % 64 == 0;
     L.kb = (int64_t)__builtin_popcountll(mask) * p->b;
     L.ld_l = (l + 7) / 8 * 8;      // BF16 rows of l elements, 16-byte aligned
     L.ld_m = (m + 7) / 8 * 8;      // BF16 rows of m elements
     L.ld_kb = (L.kb + 3) / 4 * 4;  // FP32 rows of k*b elements
     L.dc16 = align256((size_t)m * L.ld_l * 2);
-    L.bsel = align256((size_t)L.kb * L.ld_l * 2);
+    L.bsel = L.mn ? 0 : align256((size_t)L.kb * L.ld_l * 2);
     L.t = align256((size_t)m * L.ld_kb * 4);
-    L.asel = align256((size_t)L.kb * L.ld_m * 2);
-    L.dct16 = align256((size_t)l * L.ld_m * 2);
+    L.asel = L.mn ? 0 : align256((size_t)L.kb * L.ld_m * 2);
+    L.dct16 = L.mn ? 0 : align256((size_t)l * L.ld_m * 2);
     L.u = align256((size_t)L.kb * ((l + 3) / 4 * 4) * 4);
     return L;
 }
 
 size_t backward_bytes(const BackwardLayout &L, bool need_dx, bool need_dg) {
-    return (need_dx ? L.dc16 + L.bsel + L.t : 0) + (need_dg ? L.asel + L.dct16 + L.u : 0) + 256;
+    return L.dc16 + (need_dx ? L.bsel + L.t : 0) + (need_dg ? L.asel + L.dct16 + L.u : 0) + 256;
 }
 
 }  // namespace
@@ -534,18 +543,24 @@ extern "C" os_status oversketch_matmul_backward(oversketch_plan_t plan, const vo
     if (!dC && m > 0 && l > 0) return OS_ERR_INVALID_ARG;
     const float inv_k = 1.0f / (float)__builtin_popcountll(mask);
     char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(workspace) + 255) & ~uintptr_t(255));
+    cudaStream_t st = as_stream(stream);
+    void *dc16 = base;
+    base += L.dc16;
+    if (m > 0 && l > 0 && (need_dx || L.mn)) OSK_TRY(oversketch_cast(dC, OS_F32, m, l, lddc, dc16, OS_BF16, L.ld_l, stream));
     if (need_dx) {
         if (l > 0 && !BtT) return OS_ERR_INVALID_ARG;
-        void *dc16 = base;
-        void *bsel = base + L.dc16;
-        float *T = reinterpret_cast<float *>(base + L.dc16 + L.bsel);
-        base += L.dc16 + L.bsel + L.t;
-        if (l > 0) {
-            OSK_TRY(oversketch_cast(dC, OS_F32, m, l, lddc, dc16, OS_BF16, L.ld_l, stream));
+        void *bsel = base;
+        float *T = reinterpret_cast<float *>(base + L.bsel);
+        base += L.bsel + L.t;
+        if (l > 0 && L.mn) {
+            // T = dC B~_sel^T: B~^T (l x z) read MN-major, kept blocks picked by column
+            OSK_TRY(gemm_bf16_mn(dc16, L.ld_l, false, BtT, ldbt, true, m, L.kb, l, inv_k, T, L.ld_kb, p->b, 2, mask,
+                                 p->P, st));
+        } else if (l > 0) {
             OSK_TRY(oversketch_select_transpose(BtT, OS_BF16, l, z, ldbt, mask, p->b, bsel, OS_BF16, L.ld_l, stream));
             OSK_TRY(oversketch_gemm_bf16(dc16, L.ld_l, bsel, L.ld_l, m, L.kb, l, inv_k, 0.0f, T, L.ld_kb, stream));
         } else {
-            OSK_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)m * L.ld_kb * 4, as_stream(stream)));
+            OSK_CUDA_TRY(cudaMemsetAsync(T, 0, (size_t)m * L.ld_kb * 4, st));
         }
         OSK_TRY(oversketch_unsketch_cols(plan, T, m, L.ld_kb, mask, 1.0f, dX, x_t, ldx, stream));
     }
@@ -555,12 +570,16 @@ extern "C" os_status oversketch_matmul_backward(oversketch_plan_t plan, const vo
         void *dct16 = base + L.asel;
         float *U = reinterpret_cast<float *>(base + L.asel + L.dct16);
         const int64_t ldu = (l + 3) / 4 * 4;
-        if (m > 0) {
+        if (m > 0 && L.mn) {
+            // U = A~_sel^T dC: A~ (m x z, kept blocks picked by column) and dC read MN-major
+            OSK_TRY(gemm_bf16_mn(At, ldat, true, dc16, L.ld_l, true, L.kb, l, m, inv_k, U, ldu, p->b, 1, mask, p->P,
+                                 st));
+        } else if (m > 0) {
             OSK_TRY(oversketch_select_transpose(At, OS_BF16, m, z, ldat, mask, p->b, asel, OS_BF16, L.ld_m, stream));
             OSK_TRY(oversketch_select_transpose(dC, OS_F32, m, l, lddc, 0, 0, dct16, OS_BF16, L.ld_m, stream));
             OSK_TRY(oversketch_gemm_bf16(asel, L.ld_m, dct16, L.ld_m, L.kb, l, m, inv_k, 0.0f, U, ldu, stream));
         } else {
-            OSK_CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)L.kb * ldu * 4, as_stream(stream)));
+            OSK_CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)L.kb * ldu * 4, st));
         }
         OSK_TRY(oversketch_unsketch_rows(plan, U, l, ldu, mask, 1.0f, dG, g_t, ldg, stream));
     }

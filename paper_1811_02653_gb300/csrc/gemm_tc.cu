@@ -126,6 +126,11 @@ struct GemmArgs {
     // CTA-pair kernel, C = A A^T (B is A): only the tile pairs on and below the
     // diagonal are computed; each off-diagonal one is also stored transposed
     int32_t sym;
+    // CTA-pair kernel with MN-major operands: for the operands flagged in mn_remap
+    // (1: A, 2: B) row/column q of C comes from column mn_kept[q / mn_b] * mn_b +
+    // q % mn_b of the operand (its listed blocks of width mn_b, P of them stored)
+    int32_t mn_b, mn_remap;
+    BlockList mn_kept;
 };
 
 // Tile pair t of the lower triangle (row-major: pair row pm, tile column tn <= pm).
@@ -585,11 +590,17 @@ struct CfgPair {
     static_assert(SMEM <= 232448, "shared memory");
 };
 
+// kAMN / kBMN: A (M x K) or B (N x K) is read MN-major: stored K rows by MN
+// columns (MN contiguous), loaded as 64 x 64 boxes, 64-element MN chunks of 8 KB
+// in the stage; the MN coordinate goes through g.mn_kept when g.mn_b > 0.
+template <bool kAMN, bool kBMN>
 __global__ void __launch_bounds__(CfgPair::THREADS, 1)
 gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
                       const GemmArgs g) {
     using C = CfgPair;
     constexpr int STAGES = C::STAGES, BN = C::BN, BKE = C::BKE;
+    constexpr uint32_t kChunk = 64 * ROWB;   // one 64-element MN chunk: 64 K rows of 128 B
+    constexpr uint32_t kIdesc = C::IDESC | (kAMN ? 1u << 15 : 0u) | (kBMN ? 1u << 16 : 0u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *tiles = smem;
@@ -645,6 +656,16 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
     auto tile_num_kb = [&](uint64_t msk) -> int {
         return g.block_masks ? __popcll(msk) * g.kb_per_blk : g.num_kb;
     };
+    // MN coordinate of row/column q of C (extent `ext`) in an MN-major operand;
+    // `remap`: through the listed blocks, and rows past the extent at column
+    // P * mn_b, past the stored blocks (the load fills zeros there as it does
+    // past the extent of an operand that is not remapped)
+    auto mn_coord = [&](int64_t q, int64_t ext, bool remap) -> int {
+        if (!remap) return (int)q;
+        if (q >= ext) return (int)((int64_t)g.P * g.mn_b);
+        const int64_t blk = q / g.mn_b;
+        return (int)((int64_t)g.mn_kept.idx[blk] * g.mn_b + (q - blk * g.mn_b));
+    };
 
     if (warp == 0) {
         // ---------------- TMA producer (this CTA's half of every stage) ----------------
@@ -678,8 +699,21 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
                     uint8_t *st = tiles + stage * C::STAGE_BYTES;
                     const uint32_t fb = cluster_addr(&full[stage], 0);
                     if (leader) mbar_expect_tx(&full[stage], C::PAIR_TX);
-                    tma_load_2d_pair(&tmap_a, fb, st, kz, tm * BM);
-                    tma_load_2d_pair(&tmap_b, fb, st + C::A_BYTES, kz, tn * BN + rank * (BN / 2));
+                    if constexpr (kAMN) {
+                        for (int h = 0; h < BM / 64; ++h)
+                            tma_load_2d_pair(&tmap_a, fb, st + h * kChunk,
+                                             mn_coord((int64_t)tm * BM + 64 * h, g.m, g.mn_remap & 1), kz);
+                    } else {
+                        tma_load_2d_pair(&tmap_a, fb, st, kz, tm * BM);
+                    }
+                    if constexpr (kBMN) {
+                        for (int h = 0; h < BN / 128; ++h)
+                            tma_load_2d_pair(&tmap_b, fb, st + C::A_BYTES + h * kChunk,
+                                             mn_coord((int64_t)tn * BN + rank * (BN / 2) + 64 * h, g.l,
+                                                      g.mn_remap & 2), kz);
+                    } else {
+                        tma_load_2d_pair(&tmap_b, fb, st + C::A_BYTES, kz, tn * BN + rank * (BN / 2));
+                    }
                     issued[stage] = true;
                     issued_phase[stage] = phase;
                     if (++stage == STAGES) stage = 0, phase ^= 1u;
@@ -717,9 +751,15 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
                         const uint32_t sa0 = smem_u32(tiles + stage * C::STAGE_BYTES);
                         const uint32_t sb0 = sa0 + C::A_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < ROWB / 32; ++kk)
-                            umma_f16_pair(d, sdesc_kmajor_sw128(sa0 + kk * 32), sdesc_kmajor_sw128(sb0 + kk * 32),
-                                          C::IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < ROWB / 32; ++kk) {
+                            // a K slice of 16: 32 bytes into each K-major row, or 16 rows
+                            // of an MN-major chunk
+                            const uint64_t da = kAMN ? sdesc_mnmajor_sw128(sa0 + kk * 16 * ROWB, kChunk)
+                                                     : sdesc_kmajor_sw128(sa0 + kk * 32);
+                            const uint64_t db = kBMN ? sdesc_mnmajor_sw128(sb0 + kk * 16 * ROWB, kChunk)
+                                                     : sdesc_kmajor_sw128(sb0 + kk * 32);
+                            umma_f16_pair(d, da, db, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        }
                         umma_commit_pair(&empty[stage], 0x3);   // the stage is free in both CTAs
                     }
                     __syncwarp();
@@ -933,6 +973,9 @@ os_status launch_tc(const void *A0, const void *A1, int64_t lda, const void *B0,
     return check_launch();
 }
 
+template <bool kAMN, bool kBMN>
+os_status launch_pair_args(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g, cudaStream_t st);
+
 // BF16 on CTA pairs (gemm_pair_bf16_kernel): 256 x 256 tiles, two SMs each.
 // C = A A^T (B the same matrix as A) is symmetric: only the lower triangle of
 // tile pairs is computed and mirrored.
@@ -969,12 +1012,20 @@ os_status launch_pair_bf16(const void *A, int64_t lda, const void *B, int64_t ld
     CUtensorMap ta, tb;
     OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, zK, lda, BM, C::BKE));
     OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, zK, ldb, C::BN / 2, C::BKE));
-    static bool attr_set = false;
-    if (!attr_set) {
-        OSK_CUDA_TRY(cudaFuncSetAttribute(gemm_pair_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)C::SMEM));
-        attr_set = true;
-    }
+    return launch_pair_args<false, false>(ta, tb, g, st);
+}
+
+// The pair kernel with prepared arguments: one CTA pair per two SMs, persistent.
+template <bool kAMN, bool kBMN>
+os_status launch_pair_args(const CUtensorMap &ta, const CUtensorMap &tb, const GemmArgs &g, cudaStream_t st) {
+    using C = CfgPair;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(gemm_pair_bf16_kernel<kAMN, kBMN>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
+    OSK_CUDA_TRY(attr_err);
     const int pairs = num_sms() / 2;
     const int grid = 2 * (g.num_tiles < pairs ? g.num_tiles : pairs);
     cudaLaunchConfig_t cfg = {};
@@ -989,8 +1040,54 @@ os_status launch_pair_bf16(const void *A, int64_t lda, const void *B, int64_t ld
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    OSK_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_pair_bf16_kernel, ta, tb, g));
+    OSK_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_pair_bf16_kernel<kAMN, kBMN>, ta, tb, g));
     return check_launch();
+}
+
+// C (m x l) = alpha A B^T + beta C in BF16 on CTA pairs, contraction length K,
+// with A and/or B read MN-major (stored K rows by MN columns, row pitch lda/ldb),
+// so that neither needs a transpose.  For the operands flagged in remap (1: A,
+// 2: B) row/column q of C is column kept[q / mn_b] * mn_b + q % mn_b of the
+// stored operand, whose MN extent is P * mn_b; mn_b a multiple of 64.
+os_status launch_pair_bf16_mn(const void *A, int64_t lda, bool a_mn, const void *B, int64_t ldb, bool b_mn,
+                              int64_t m, int64_t l, int64_t K, float alpha, float beta, float *Cout, int64_t ldc,
+                              int32_t mn_b, int32_t remap, const BlockList &kept, int32_t P, cudaStream_t st) {
+    using C = CfgPair;
+    if (!aligned16(A) || !aligned16(B) || (lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0) return OS_ERR_INVALID_ARG;
+    if (remap && (mn_b <= 0 || mn_b % 64 != 0 || P < 1)) return OS_ERR_INVALID_ARG;
+    if (K <= 0 || K >= (int64_t(1) << 31) || m >= (int64_t(1) << 30) || l >= (int64_t(1) << 30))
+        return OS_ERR_UNSUPPORTED;
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    const int64_t kpad = (K + C::BKE - 1) / C::BKE * C::BKE;
+    g.m = m;
+    g.l = l;
+    g.b = (int32_t)kpad;
+    g.kb_per_blk = (int32_t)(kpad / C::BKE);
+    g.kept.count = 1;   // one K block, [0, kpad): the loads fill zeros past K
+    g.num_kb = g.kb_per_blk;
+    g.tiles_m = (int)((m + BM - 1) / BM);
+    g.tiles_n = (int)((l + C::BN - 1) / C::BN);
+    g.num_tiles = (g.tiles_m + 1) / 2 * g.tiles_n;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.C = Cout;
+    g.ldc = ldc;
+    g.P = P;
+    g.mn_b = mn_b;
+    g.mn_remap = remap;
+    g.mn_kept = kept;
+    const int64_t a_ext = (remap & 1) ? (int64_t)P * mn_b : m;   // stored MN extents
+    const int64_t b_ext = (remap & 2) ? (int64_t)P * mn_b : l;
+    CUtensorMap ta, tb;
+    if (a_mn) OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, K, a_ext, lda, 64, 64));
+    else OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, K, lda, BM, C::BKE));
+    if (b_mn) OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, K, b_ext, ldb, 64, 64));
+    else OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, K, ldb, C::BN / 2, C::BKE));
+    if (a_mn && b_mn) return launch_pair_args<true, true>(ta, tb, g, st);
+    if (a_mn) return launch_pair_args<true, false>(ta, tb, g, st);
+    if (b_mn) return launch_pair_args<false, true>(ta, tb, g, st);
+    return launch_pair_args<false, false>(ta, tb, g, st);
 }
 
 os_status launch_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t m, int64_t l, int64_t zK,
@@ -1000,6 +1097,16 @@ os_status launch_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, in
 }
 
 }  // namespace
+
+// The backward pass's products straight from the sketched operands: T = dC
+// B~_sel^T (B~^T read MN-major, its kept blocks picked by column) and U =
+// A~_sel^T dC (A~ and dC read MN-major).  See launch_pair_bf16_mn.
+os_status gemm_bf16_mn(const void *A, int64_t lda, bool a_mn, const void *B, int64_t ldb, bool b_mn, int64_t m,
+                       int64_t l, int64_t K, float alpha, float *C, int64_t ldc, int32_t mn_b, int32_t remap,
+                       uint64_t mask, int32_t P, cudaStream_t st) {
+    const BlockList kept = mask_to_list(mask ? mask : ~0ull, P);
+    return launch_pair_bf16_mn(A, lda, a_mn, B, ldb, b_mn, m, l, K, alpha, 0.0f, C, ldc, mn_b, remap, kept, P, st);
+}
 
 os_status gemm_masked_tc(const Plan *p, const void *At, int64_t ldat, const float *a_scales,
                          const void *BtT, int64_t ldbt, const float *b_scales, os_dtype dt, int64_t m,

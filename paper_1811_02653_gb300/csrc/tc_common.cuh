@@ -214,7 +214,22 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor for kind::f16 (BF16 x BF16 -> F32), both K-major.
+// The same for an MN-major operand with 128-byte swizzle: rows are K, each 128-byte
+// row holds 64 BF16 of M (or N); the tile is stored as 64-element MN chunks of
+// `chunk_bytes` each (all its K rows), so the leading byte offset (MN direction)
+// is the chunk size and the stride byte offset (K direction) 8 rows * 128 B.
+__device__ __forceinline__ uint64_t sdesc_mnmajor_sw128(uint32_t saddr, uint32_t chunk_bytes) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
+    d |= (uint64_t)((chunk_bytes >> 4) & 0x3FFFu) << 16;   // leading byte offset: next 64 of MN
+    d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: next 8 rows of K
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor for kind::f16 (BF16 x BF16 -> F32), both K-major (bits 15
+// and 16 set mark A or B as MN-major).
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                 // D format F32
            | (1u << 7)               // A format BF16

@@ -90,6 +90,32 @@ def test_autograd_small_parity(ops, ag, recompute):
     assert oracle.rel_frob(Gd.grad.cpu().numpy(), dG_ex) <= 2e-2
 
 
+@pytest.mark.parametrize("m,n,l,b,N,e,mask,sides", [
+    (300, 3000, 200, 128, 4, 1, 0b10111, "both"),   # ragged tile pairs, a dropped block between kept ones
+    (129, 2000, 77, 64, 3, 2, 0b10101, "both"),     # blocks narrower than a tile: columns picked per 64
+    (260, 4096, 300, 256, 4, 1, 0b01111, "dg"),     # dG alone (dC cast for the MN-major product only)
+    (64, 512, 64, 32, 4, 1, 0b11011, "both"),       # b not a multiple of 64: K-major copies, then the GEMMs
+])
+def test_matmul_backward_parity(ops, m, n, l, b, N, e, mask, sides):
+    # oversketch_matmul_backward from the forward's BF16 sketches: with b a multiple
+    # of 64 the tensor cores read B~^T, A~ and dC MN-major as stored; against the
+    # oracle's gradients with the same BF16 roundings
+    rng = np.random.default_rng(m + l + b)
+    X = (rng.standard_normal((m, n)) * 0.02).astype(np.float32)
+    G = (rng.standard_normal((n, l)) * 0.02).astype(np.float32)
+    dC = rng.standard_normal((m, l)).astype(np.float32)
+    p = ops.plan(n, b, N, e, 2)
+    h, s = oracle.hash_tables(n, b, N, e, 2)
+    At, _ = ops.sketch_left(p, torch.from_numpy(X).cuda(), "bf16", block_mask=mask)
+    BtT, _ = ops.sketch_right(p, torch.from_numpy(G).cuda(), "bf16", block_mask=mask)
+    dX, dG = ops.matmul_backward(p, At, BtT, torch.from_numpy(dC).cuda(), mask,
+                                 need_dx=sides == "both", need_dg=True)
+    dX_ref, dG_ref = _emulated_gradients(X, G, dC, h, s, b, mask)
+    if sides == "both":
+        assert oracle.rel_frob(dX.cpu().numpy(), dX_ref) <= 1e-4
+    assert oracle.rel_frob(dG.cpu().numpy(), dG_ref) <= 1e-4
+
+
 def test_autograd_recompute_is_bitwise_equal(ops, ag):
     m, n, l, b, N, e, mask = 128, 4096, 96, 256, 4, 1, 0b10111
     rng = np.random.default_rng(6)
