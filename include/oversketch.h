@@ -361,9 +361,10 @@ OS_API os_status oversketch_unsketch_rows(oversketch_plan_t plan, const float *U
  * blocks are read); dC: FP32 m x l (lddc).  Each side is one BF16 tensor-core
  * GEMM with FP32 accumulation (dC rounded to BF16, 1/k in the GEMM epilogue)
  * followed by an unsketch gather into dX (x_t) or dG (g_t), OS_F32 or OS_BF16.
- * With b a multiple of 64 the tensor cores read At, BtT and dC as they are laid
- * out (MN-major where the product needs it, the kept blocks picked by column);
- * otherwise the kept blocks and dC are first transposed into K-major copies.
+ * With b a multiple of 128 and m, l multiples of 8 the tensor cores read At, BtT
+ * and dC as they are laid out (MN-major where the product needs it, the kept
+ * blocks picked by column); otherwise the kept blocks and dC are first
+ * transposed into K-major copies.
  * dX or dG may be NULL: that side is skipped.  workspace: device memory of
  * oversketch_matmul_backward_workspace_size(plan, m, l, mask, dX != NULL,
  * dG != NULL) bytes (dC in BF16, any transposed copies, and the FP32 GEMM

@@ -483,8 +483,9 @@ namespace {
 
 // Workspace of the backward pass: dC in BF16 (both products use it), then T (and
 // the compacted kept blocks of B~, laid out K-major) for dX, then U (and A~'s kept
-// blocks and dC^T, K-major) for dG.  With b a multiple of 64 the tensor cores read
-// B~^T, A~ and dC MN-major as they are stored, and the K-major copies are not made.
+// blocks and dC^T, K-major) for dG.  With b a multiple of 128 and m, l multiples of
+// 8 the tensor cores read B~^T, A~ and dC MN-major as they are stored (dC's rows
+// padded to a multiple of 64), and the K-major copies are not made.
 struct BackwardLayout {
     bool mn;                         // operands read MN-major (no transposed copies)
     int64_t kb, ld_l, ld_m, ld_kb;   // padded row pitches (elements) of the BF16 / FP32 buffers
@@ -493,9 +494,9 @@ struct BackwardLayout {
 
 BackwardLayout backward_layout(const Plan *p, int64_t m, int64_t l, uint64_t mask) {
     BackwardLayout L;
-    L.mn = p->b % 64 == 0;
+    L.mn = p->b % 128 == 0 && m % 8 == 0 && l % 8 == 0;
     L.kb = (int64_t)__builtin_popcountll(mask) * p->b;
-    L.ld_l = (l + 7) / 8 * 8;      // BF16 rows of l elements, 16-byte aligned
+    L.ld_l = L.mn ? (l + 63) / 64 * 64 : (l + 7) / 8 * 8;   // BF16 rows of l elements
     L.ld_m = (m + 7) / 8 * 8;      // BF16 rows of m elements
     L.ld_kb = (L.kb + 3) / 4 * 4;  // FP32 rows of k*b elements
     L.dc16 = align256((size_t)m * L.ld_l * 2);

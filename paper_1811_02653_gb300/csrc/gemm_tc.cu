@@ -591,15 +591,17 @@ struct CfgPair {
 };
 
 // kAMN / kBMN: A (M x K) or B (N x K) is read MN-major: stored K rows by MN
-// columns (MN contiguous), loaded as 64 x 64 boxes, 64-element MN chunks of 8 KB
-// in the stage; the MN coordinate goes through g.mn_kept when g.mn_b > 0.
+// columns (MN contiguous).  One 4-D copy per operand and stage brings the CTA's
+// 128 of MN (two 64-element chunks, adjacent in memory) for the stage's 64 of K
+// as groups of 8 K rows, each group the two chunks' 1 KB atoms side by side;
+// the MN coordinate goes through g.mn_kept for the operands flagged in g.mn_remap.
 template <bool kAMN, bool kBMN>
 __global__ void __launch_bounds__(CfgPair::THREADS, 1)
 gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
                       const GemmArgs g) {
     using C = CfgPair;
     constexpr int STAGES = C::STAGES, BN = C::BN, BKE = C::BKE;
-    constexpr uint32_t kChunk = 64 * ROWB;   // one 64-element MN chunk: 64 K rows of 128 B
+    constexpr uint32_t kKGroup = 2 * 1024;   // MN-major stage: 8 K rows of both MN chunks
     constexpr uint32_t kIdesc = C::IDESC | (kAMN ? 1u << 15 : 0u) | (kBMN ? 1u << 16 : 0u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -700,17 +702,14 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
                     const uint32_t fb = cluster_addr(&full[stage], 0);
                     if (leader) mbar_expect_tx(&full[stage], C::PAIR_TX);
                     if constexpr (kAMN) {
-                        for (int h = 0; h < BM / 64; ++h)
-                            tma_load_2d_pair(&tmap_a, fb, st + h * kChunk,
-                                             mn_coord((int64_t)tm * BM + 64 * h, g.m, g.mn_remap & 1), kz);
+                        const int x = mn_coord((int64_t)tm * BM, g.m, g.mn_remap & 1);
+                        tma_load_4d_pair(&tmap_a, fb, st, 0, 0, x / 64, kz / 8);
                     } else {
                         tma_load_2d_pair(&tmap_a, fb, st, kz, tm * BM);
                     }
                     if constexpr (kBMN) {
-                        for (int h = 0; h < BN / 128; ++h)
-                            tma_load_2d_pair(&tmap_b, fb, st + C::A_BYTES + h * kChunk,
-                                             mn_coord((int64_t)tn * BN + rank * (BN / 2) + 64 * h, g.l,
-                                                      g.mn_remap & 2), kz);
+                        const int x = mn_coord((int64_t)tn * BN + rank * (BN / 2), g.l, g.mn_remap & 2);
+                        tma_load_4d_pair(&tmap_b, fb, st + C::A_BYTES, 0, 0, x / 64, kz / 8);
                     } else {
                         tma_load_2d_pair(&tmap_b, fb, st + C::A_BYTES, kz, tn * BN + rank * (BN / 2));
                     }
@@ -754,9 +753,9 @@ gemm_pair_bf16_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_c
                         for (int kk = 0; kk < ROWB / 32; ++kk) {
                             // a K slice of 16: 32 bytes into each K-major row, or 16 rows
                             // of an MN-major chunk
-                            const uint64_t da = kAMN ? sdesc_mnmajor_sw128(sa0 + kk * 16 * ROWB, kChunk)
+                            const uint64_t da = kAMN ? sdesc_mnmajor_sw128(sa0 + kk * 2 * kKGroup, 1024, kKGroup)
                                                      : sdesc_kmajor_sw128(sa0 + kk * 32);
-                            const uint64_t db = kBMN ? sdesc_mnmajor_sw128(sb0 + kk * 16 * ROWB, kChunk)
+                            const uint64_t db = kBMN ? sdesc_mnmajor_sw128(sb0 + kk * 2 * kKGroup, 1024, kKGroup)
                                                      : sdesc_kmajor_sw128(sb0 + kk * 32);
                             umma_f16_pair(d, da, db, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
                         }
@@ -895,6 +894,26 @@ os_status make_tmap(CUtensorMap *map, const void *base, CUtensorMapDataType dt, 
     CUresult r = enc(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? OS_OK : OS_ERR_INVALID_ARG;
+}
+
+// 4-D view of a matrix stored K rows by MN columns (pitch ld elements) for
+// MN-major loads: {64 of MN, 8 rows of K, MN / 64 chunks, K / 8 groups}, box
+// {64, 8, 2, 8}: two adjacent 64-element chunks for 64 rows of K, stored as 8 groups
+// of 8 rows, each group the two chunks' 1 KB atoms side by side (128-byte swizzle).
+// K % 8 == 0 and mn_ext % 64 == 0 keep every box inside the rows and columns it
+// names (past the last group or chunk the load fills zeros).
+os_status make_tmap_mn4(CUtensorMap *map, const void *base, int64_t K, int64_t mn_ext, int64_t ld) {
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return OS_ERR_CUDA;
+    if (K % 8 != 0 || mn_ext % 64 != 0 || ld < mn_ext) return OS_ERR_INVALID_ARG;
+    cuuint64_t dims[4] = {64, 8, (cuuint64_t)(mn_ext / 64), (cuuint64_t)(K / 8)};
+    cuuint64_t strides[3] = {(cuuint64_t)(ld * 2), 128, (cuuint64_t)(8 * ld * 2)};
+    cuuint32_t box[4] = {64, 8, 2, 8};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? OS_OK : OS_ERR_INVALID_ARG;
 }
 
@@ -1048,13 +1067,14 @@ os_status launch_pair_args(const CUtensorMap &ta, const CUtensorMap &tb, const G
 // with A and/or B read MN-major (stored K rows by MN columns, row pitch lda/ldb),
 // so that neither needs a transpose.  For the operands flagged in remap (1: A,
 // 2: B) row/column q of C is column kept[q / mn_b] * mn_b + q % mn_b of the
-// stored operand, whose MN extent is P * mn_b; mn_b a multiple of 64.
+// stored operand, whose MN extent is P * mn_b.  MN-major operands need K % 8 == 0,
+// a stored MN extent (and pitch) that is a multiple of 64, and mn_b % 128 == 0.
 os_status launch_pair_bf16_mn(const void *A, int64_t lda, bool a_mn, const void *B, int64_t ldb, bool b_mn,
                               int64_t m, int64_t l, int64_t K, float alpha, float beta, float *Cout, int64_t ldc,
                               int32_t mn_b, int32_t remap, const BlockList &kept, int32_t P, cudaStream_t st) {
     using C = CfgPair;
     if (!aligned16(A) || !aligned16(B) || (lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0) return OS_ERR_INVALID_ARG;
-    if (remap && (mn_b <= 0 || mn_b % 64 != 0 || P < 1)) return OS_ERR_INVALID_ARG;
+    if (remap && (mn_b <= 0 || mn_b % 128 != 0 || P < 1)) return OS_ERR_INVALID_ARG;
     if (K <= 0 || K >= (int64_t(1) << 31) || m >= (int64_t(1) << 30) || l >= (int64_t(1) << 30))
         return OS_ERR_UNSUPPORTED;
     GemmArgs g;
@@ -1077,12 +1097,14 @@ os_status launch_pair_bf16_mn(const void *A, int64_t lda, bool a_mn, const void 
     g.mn_b = mn_b;
     g.mn_remap = remap;
     g.mn_kept = kept;
-    const int64_t a_ext = (remap & 1) ? (int64_t)P * mn_b : m;   // stored MN extents
-    const int64_t b_ext = (remap & 2) ? (int64_t)P * mn_b : l;
+    // stored MN extents (an operand that is not remapped: its pitch must reach the
+    // next multiple of 64; those columns only feed rows/columns of C past m or l)
+    const int64_t a_ext = (remap & 1) ? (int64_t)P * mn_b : (m + 63) / 64 * 64;
+    const int64_t b_ext = (remap & 2) ? (int64_t)P * mn_b : (l + 63) / 64 * 64;
     CUtensorMap ta, tb;
-    if (a_mn) OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, K, a_ext, lda, 64, 64));
+    if (a_mn) OSK_TRY(make_tmap_mn4(&ta, A, K, a_ext, lda));
     else OSK_TRY(make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, m, K, lda, BM, C::BKE));
-    if (b_mn) OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, K, b_ext, ldb, 64, 64));
+    if (b_mn) OSK_TRY(make_tmap_mn4(&tb, B, K, b_ext, ldb));
     else OSK_TRY(make_tmap(&tb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, l, K, ldb, C::BN / 2, C::BKE));
     if (a_mn && b_mn) return launch_pair_args<true, true>(ta, tb, g, st);
     if (a_mn) return launch_pair_args<true, false>(ta, tb, g, st);

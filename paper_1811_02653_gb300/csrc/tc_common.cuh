@@ -142,6 +142,17 @@ __device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap *map, uint32_
         : "memory");
 }
 
+// A 4-D box into this CTA's shared memory, completion on the leader's barrier.
+__device__ __forceinline__ void tma_load_4d_pair(const CUtensorMap *map, uint32_t cluster_bar, void *dst, int c0,
+                                                 int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(cluster_bar), "r"(c0), "r"(c1), "r"(c2),
+          "r"(c3)
+        : "memory");
+}
+
 // Wait with acquire at cluster scope (the phase may be completed by the other CTA).
 __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
@@ -215,14 +226,14 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
 }
 
 // The same for an MN-major operand with 128-byte swizzle: rows are K, each 128-byte
-// row holds 64 BF16 of M (or N); the tile is stored as 64-element MN chunks of
-// `chunk_bytes` each (all its K rows), so the leading byte offset (MN direction)
-// is the chunk size and the stride byte offset (K direction) 8 rows * 128 B.
-__device__ __forceinline__ uint64_t sdesc_mnmajor_sw128(uint32_t saddr, uint32_t chunk_bytes) {
+// row holds 64 BF16 of M (or N), in atoms of 8 rows (1 KB); the leading byte offset
+// is the distance between atoms along MN (the next 64 of MN), the stride byte
+// offset the distance between atoms along K (the next 8 rows).
+__device__ __forceinline__ uint64_t sdesc_mnmajor_sw128(uint32_t saddr, uint32_t mn_stride, uint32_t k_stride) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
-    d |= (uint64_t)((chunk_bytes >> 4) & 0x3FFFu) << 16;   // leading byte offset: next 64 of MN
-    d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: next 8 rows of K
+    d |= (uint64_t)((mn_stride >> 4) & 0x3FFFu) << 16;   // leading byte offset: next 64 of MN
+    d |= (uint64_t)((k_stride >> 4) & 0x3FFFu) << 32;    // stride byte offset: next 8 rows of K
     d |= (uint64_t)1 << 46;                          // descriptor version
     d |= (uint64_t)2 << 61;                          // 128-byte swizzle
     return d;

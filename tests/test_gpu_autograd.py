@@ -91,15 +91,17 @@ def test_autograd_small_parity(ops, ag, recompute):
 
 
 @pytest.mark.parametrize("m,n,l,b,N,e,mask,sides", [
-    (300, 3000, 200, 128, 4, 1, 0b10111, "both"),   # ragged tile pairs, a dropped block between kept ones
-    (129, 2000, 77, 64, 3, 2, 0b10101, "both"),     # blocks narrower than a tile: columns picked per 64
-    (260, 4096, 300, 256, 4, 1, 0b01111, "dg"),     # dG alone (dC cast for the MN-major product only)
-    (64, 512, 64, 32, 4, 1, 0b11011, "both"),       # b not a multiple of 64: K-major copies, then the GEMMs
+    (296, 3000, 200, 128, 4, 1, 0b10111, "both"),   # MN-major: ragged tile pairs, dC rows padded to 64
+    (520, 4096, 328, 256, 3, 2, 0b10101, "both"),   # MN-major: blocks of two tile columns, two dropped
+    (264, 4096, 304, 256, 4, 1, 0b01111, "dg"),     # MN-major dG alone (dC cast for it only)
+    (300, 3000, 200, 128, 4, 1, 0b10111, "both"),   # m not a multiple of 8: K-major copies
+    (129, 2000, 77, 64, 3, 2, 0b10101, "both"),     # b = 64: K-major copies
+    (64, 512, 64, 32, 4, 1, 0b11011, "both"),       # b = 32: K-major copies
 ])
 def test_matmul_backward_parity(ops, m, n, l, b, N, e, mask, sides):
     # oversketch_matmul_backward from the forward's BF16 sketches: with b a multiple
-    # of 64 the tensor cores read B~^T, A~ and dC MN-major as stored; against the
-    # oracle's gradients with the same BF16 roundings
+    # of 128 and m, l multiples of 8 the tensor cores read B~^T, A~ and dC MN-major
+    # as stored; against the oracle's gradients with the same BF16 roundings
     rng = np.random.default_rng(m + l + b)
     X = (rng.standard_normal((m, n)) * 0.02).astype(np.float32)
     G = (rng.standard_normal((n, l)) * 0.02).astype(np.float32)
