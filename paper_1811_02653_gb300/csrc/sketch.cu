@@ -506,7 +506,7 @@ __device__ __forceinline__ float row_of(const typename RowVec<R>::T &v, int r) {
 }
 
 template <typename OutT, int R>
-__global__ void __launch_bounds__(512) unsketch_cols_smem_kernel(
+__global__ void __launch_bounds__(1024) unsketch_cols_smem_kernel(
     const float *__restrict__ T, int64_t m, int64_t ldt, int64_t kb, const uint32_t *__restrict__ hs, int64_t n,
     int32_t b, BlockList kept, float scale, OutT *__restrict__ dX, int64_t ldx) {
     using V = typename RowVec<R>::T;
@@ -1065,7 +1065,7 @@ os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t l
     if (m == 0) return OS_OK;   // an empty dX
     if (!T || !dX) return OS_ERR_INVALID_ARG;
     const BlockList kept = mask_to_list(mask, p->P);
-    // rows of T staged per CTA (512 threads): 4, 2 or 1, the most that fit in
+    // rows of T staged per CTA (1024 threads): 4, 2 or 1, the most that fit in
     // 200 KB, else the unstaged kernel
     const int64_t kb = (int64_t)kcnt * p->b;
     const size_t row_bytes = (size_t)kb * sizeof(float);
@@ -1076,7 +1076,7 @@ os_status unsketch_cols_impl(const Plan *p, const float *T, int64_t m, int64_t l
         auto launch = [&](auto kern, auto *out) -> os_status {
             if (smem > 48 * 1024)
                 OSK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<gxs, 512, smem, st>>>(T, m, ldt, kb, p->hs, p->n, p->b, kept, scale, out, ldx);
+            kern<<<gxs, 1024, smem, st>>>(T, m, ldt, kb, p->hs, p->n, p->b, kept, scale, out, ldx);
             return check_launch();
         };
         if (x_t == OS_F32) {
