@@ -43,7 +43,7 @@ METRIC = "sketched A·B effective TFLOP/s (2mnl/t) vs exact GEMM at stated Frobe
 # DRAM bytes (read + write) of one gemm_pair_bf16_kernel launch on the square workload:
 # one ncu capture of the 8192 x 8192 x 8192 product (--shape 8192,65536,8192), scaled by
 # the 4x tiles of the full 16384 x 8192 x 16384 product (profiles/square_launch_list.md)
-TRAFFIC_GEMM_PAIR_SQUARE = 4 * (1283784448 + 254658304)
+TRAFFIC_GEMM_PAIR_SQUARE = 4 * (1280785000 + 255578368)
 UNIT = "TFLOP/s"
 
 
