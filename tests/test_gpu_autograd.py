@@ -94,6 +94,7 @@ def test_autograd_small_parity(ops, ag, recompute):
     (296, 3000, 200, 128, 4, 1, 0b10111, "both"),   # MN-major: ragged tile pairs, dC rows padded to 64
     (520, 4096, 328, 256, 3, 2, 0b10101, "both"),   # MN-major: blocks of two tile columns, two dropped
     (264, 4096, 304, 256, 4, 1, 0b01111, "dg"),     # MN-major dG alone (dC cast for it only)
+    (8, 640, 8, 128, 2, 1, 0b010, "both"),          # MN-major, tiny: one kept block of 128, tiles mostly past the extents
     (300, 3000, 200, 128, 4, 1, 0b10111, "both"),   # m not a multiple of 8: K-major copies
     (129, 2000, 77, 64, 3, 2, 0b10101, "both"),     # b = 64: K-major copies
     (64, 512, 64, 32, 4, 1, 0b11011, "both"),       # b = 32: K-major copies
