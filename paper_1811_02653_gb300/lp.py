@@ -86,7 +86,9 @@ class SketchedBarrierLP:
     def hessian(self, s: torch.Tensor, block_masks) -> torch.Tensor:
         """A^T diag(1/s^2) A through the sketch: (S^T D^{1/2} A)^T, then the
         masked-block products, block (i, j) keeping the sketch blocks of
-        block_masks[i, j].  With `exact`, the unsketched BF16 product instead."""
+        block_masks[i, j].  With `exact`, the unsketched BF16 product instead.
+        When every block keeps the same set the product is a Gram matrix and the
+        library computes its lower triangle only (one mask, the same operand twice)."""
         d = (1.0 / s).float()
         if self.exact:
             if self.At is None:
@@ -94,7 +96,10 @@ class SketchedBarrierLP:
             Xd = (self.At * d).to(torch.bfloat16)
             return ops.gemm_bf16(Xd, Xd, C=self.H)
         ops.sketch_right(self.plan, self.A, "bf16", out=self.Ask, workspace=self.ws, row_scale=d)
-        masks = torch.as_tensor(np.asarray(block_masks, dtype=np.int64)).to(self.device, non_blocking=True)
+        bm = np.asarray(block_masks, dtype=np.int64)
+        if bm.size and (bm == bm.flat[0]).all():
+            return ops.gemm_masked(self.plan, self.Ask, self.Ask, int(bm.flat[0]), C=self.H)
+        masks = torch.as_tensor(bm).to(self.device, non_blocking=True)
         return ops.gemm_masked_blocks(self.plan, self.Ask, self.Ask, masks, self.blk, self.blk, C=self.H)
 
     # -- the Newton system ----------------------------------------------------
