@@ -44,6 +44,10 @@ METRIC = "sketched A·B effective TFLOP/s (2mnl/t) vs exact GEMM at stated Frobe
 # one ncu capture of the 8192 x 8192 x 8192 product (--shape 8192,65536,8192), scaled by
 # the 4x tiles of the full 16384 x 8192 x 16384 product (profiles/square_launch_list.md)
 TRAFFIC_GEMM_PAIR_SQUARE = 4 * (1280785000 + 255578368)
+# DRAM bytes (read + write) of sketch_left_onepass_kernel on the first 304 rows of the
+# interior-point operand (--workload hessian --rows 304; profiles/sketch_left_onepass_304x1048576.md):
+# the kernel streams each row once, so a launch over m rows moves m / 304 times as much
+TRAFFIC_ONEPASS_304_ROWS = 1298136000 + 19260672
 UNIT = "TFLOP/s"
 
 
@@ -781,10 +785,18 @@ def run_hessian(args):
     t_sk = per[phases[0][0]]
     sk_bytes = w.m * w.n * 4 + w.n * 4 + w.m * w.k * w.b * 2
     roof = _hbm_roof(peaks, peak_kind, sk_bytes, t_sk, f"{sk_kernel} (left sketch)")
+    if not args.dense_sketch:
+        roof["traffic"] = TRAFFIC_ONEPASS_304_ROWS * w.m / 304
+        roof["traffic_note"] = "sketch_left_onepass_kernel, ncu capture of 304 rows scaled by rows"
     gemm_flop = 2.0 * w.m * w.k * w.b * w.m
+    # the symmetric product computes the 256 x 256 tiles on and below the diagonal only
+    T = -(-w.m // 256)
+    done_flop = gemm_flop * (T * (T + 1) / 2) / (T * T)
     t_g = per[phases[1][0]]
-    gemm = {"tflops": gemm_flop / (t_g * 1e-3) / 1e12,
-            "frac_of_sustained_bf16": gemm_flop / (t_g * 1e-3) / 1e12 / peaks.get("bf16_tflops_sustained", 1710.4)}
+    gemm = {"tflops_effective": gemm_flop / (t_g * 1e-3) / 1e12,
+            "tflops_executed": done_flop / (t_g * 1e-3) / 1e12,
+            "frac_of_sustained_bf16": done_flop / (t_g * 1e-3) / 1e12 / peaks.get("bf16_tflops_sustained", 1710.4),
+            "note": f"lower triangle: {T * (T + 1) // 2} of {T * T} tiles of 256 x 256 computed, then mirrored"}
     err, cpu = None, None
     if _cpu_leg(args, rank, world):
         import oracle
