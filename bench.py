@@ -734,7 +734,7 @@ def run_small(args):
     line = _line(args, w.name, _job_value(flop, fl_ms, world), fl_ms, gd, cfg, fl_per, roof, cpu,
                  {"value": _job_value(flop, e2e_ms, world), "unit": UNIT, "ms_per_step": e2e_ms,
                   "h2d_bytes_per_step": A_h.numel() * 4 + B_h.numel() * 4, "d2h_bytes_per_step": C_h.numel() * 4},
-                 3 * args.steps, clk, err, world,
+                 4 * args.steps, clk, err, world,   # transpose + gather, gather in place, GEMM
                  warm_l2={"ms_per_step": warm_ms, "tflops": _job_value(flop, warm_ms, world),
                           "phases_ms": {k_: round(v_, 4) for k_, v_ in warm_per.items()}},
                  plan_ms=_plan_record(plan_s, plan_dev))
@@ -1149,7 +1149,8 @@ def run_sec51(args):
                        f"4 of 30 blocks ignored per {blk}x{blk} block of C",
            "m": m, "n": n, "l": l, "b": blk, "P": P, "e_per_block": 4, "gemm_dtype": "bf16", "input_dtype": "f32",
            "l2": "A and B (10 GB each) larger than L2; no flush needed", "parallelism": f"replicas{world}"}
-    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, cpu, None, 3 * args.steps, clk, err,
+    # transpose + gather (left), gather in place (right), per-block GEMM
+    line = _line(args, cfg["workload"], value, ms, "bf16", cfg, per, roof, cpu, None, 4 * args.steps, clk, err,
                  world)
     if rank == 0:
         print(json.dumps(line), flush=True)
